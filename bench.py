@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark of MTGP generation on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c2|c1|c3|c4]
+
+A step is one pass of the whole generation path over one batch: for the
+default workload (C2) every one of 128 MTGP11213 parameter sets produces 2^24
+numbers in each of uint32, float [1,2) and float [0,1) -- 384 generator
+instances, one thread block each, in one launch (about 24 GiB written).  The
+step continues every generator's stream, so successive steps do new work.
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own shard
+(distinct generator IDs, same sizes: weak scaling, no collective on the data
+path); the time is the max over ranks.  `--impl reference` times the CPU oracle
+on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MTGP Gnum/s & HBM write GB/s vs peak (plain vs batched); served p50/p99 latency"
+KERNEL_SOURCES = ["paper_1005_4973_gb300/csrc/mtgp_kernels.cu", "paper_1005_4973_gb300/csrc/mtgp_internal.h"]
+NCU_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(name: str, rank: int):
+    from paper_1005_4973_gb300 import workloads as WL
+    wl = {"c1": WL.c1, "c2": WL.c2, "c3": WL.c3, "c4": WL.c4,
+          "c2s": lambda: WL.c2(n=1 << 20)}[name]()
+    if rank:
+        for g in wl.gens:                  # distinct streams per rank
+            g.gen_id += rank * 1_000_000
+            g.seed += rank
+    return wl
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.samples, self.proc, self.marks = [], None, []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append((time.perf_counter(), parts))
+
+    def mark(self):
+        self.marks.append(time.perf_counter())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [p for t, p in self.samples if t0 <= t <= t1]
+        window = "timed region"
+        if len(rows) < 3:                   # short region: widen to the loaded run around it
+            rows = [p for t, p in self.samples if self.marks and self.marks[0] <= t <= t1]
+            window = "warm-up and timed region"
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(rows[0][1]),
+                "power_w_max": max((num(r[2]) or 0.0) for r in rows), "reasons": reasons,
+                "samples": len(rows), "window": window}
+
+
+def cpu_baseline(wl, numbers_per_gen: int, batch: int = 64):
+    """The oracle, as it stands, on the host cores over a bounded sample."""
+    import oracle as O
+    O.build()
+    threads = os.cpu_count() or 1
+    specs = wl.gens
+    dts = {r[0]: r[1] for r in wl.requests}
+    t0 = time.perf_counter()
+    done = 0
+    for b in range(0, len(specs), batch):
+        ps, sts = [], []
+        for g in specs[b:b + batch]:
+            p = O.params_draw(g.mexp, g.param_seed, g.id)
+            ps.append(p)
+            sts.append(O.seed_state(p, g.gen_id, g.seed))
+        O.generate_many(ps, sts, [numbers_per_gen] * len(ps), [dts[b + i] for i in range(len(ps))], threads)
+        done += numbers_per_gen * len(ps)
+    dt = time.perf_counter() - t0
+    return done / dt / 1e9, threads, dt, done
+
+
+def run_reference(args, rank, world):
+    """`--impl reference`: the CPU oracle timed on the host cores (rank 0)."""
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    wl = workload(args.workload, 0)
+    per_step = args.ref_numbers
+    threads = os.cpu_count() or 1
+    ps, sts, dts = [], [], []
+    for r in wl.requests:
+        g = wl.gens[r[0]]
+        p = O.params_draw(g.mexp, g.param_seed, g.id)
+        ps.append(p)
+        sts.append(O.seed_state(p, g.gen_id, g.seed))
+        dts.append(r[1])
+
+    def step():
+        O.generate_many(ps, sts, [per_step] * len(ps), dts, threads)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    nums = per_step * len(ps) * args.steps
+    value = nums / dt / 1e9
+    sample = f"{len(ps)} generator instances of {wl.name} x {per_step} numbers per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gnum/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": wl.name, "generators": len(ps)},
+        "cpu_baseline": {"value": value, "unit": "Gnum/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Gnum/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c2s"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-numbers", type=int, default=1 << 22, help="numbers per generator in the CPU sample")
+    ap.add_argument("--ref-numbers", type=int, default=1 << 16, help="numbers per generator per reference step")
+    ap.add_argument("--config", default="", help="JSON launch config overrides (threads, words_per_round, ...)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_1005_4973_gb300 as M
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    wl = workload(args.workload, rank)
+    ps = [M.mtgp_params_draw(g.mexp, g.param_seed, g.id) for g in wl.gens]
+    pool = M.Pool(ps, [g.gen_id for g in wl.gens], [g.seed for g in wl.gens])
+    if args.workload == "c4":
+        pool.set_config(persistent=1)
+    if args.config:
+        pool.set_config(**json.loads(args.config))
+    cfg = pool.config.as_dict()
+    total = wl.total_numbers
+    out = torch.empty(total, dtype=torch.int32, device="cuda")
+    reqs = wl.requests
+    stream = torch.cuda.current_stream()
+
+    # write-only roofline probe on the same buffer
+    probe_words = (min(total, 1 << 31) // 4) * 4
+    for _ in range(3):
+        M.mtgp_fill_probe(out, probe_words)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for _ in range(5):
+        M.mtgp_fill_probe(out, probe_words)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    write_probe_gbs = 5 * 4 * probe_words / (pe0.elapsed_time(pe1) * 1e-3) / 1e9
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_id = vis.split(",")[local].strip() if vis else str(local)
+    sampler = ClockSampler(smi_id) if rank == 0 else None
+    if sampler:
+        time.sleep(0.3)
+        sampler.mark()
+    for _ in range(args.warmup):
+        pool.generate(reqs, out)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_host0 = time.perf_counter()
+    e0.record(stream)
+    for k in range(args.steps):
+        starts[k].record(stream)
+        pool.generate(reqs, out)
+        ends[k].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_host1 = time.perf_counter()
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    clocks = sampler.summary(t_host0, t_host1) if sampler else None
+
+    numbers_all = total * args.steps * world
+    value = numbers_all / (ms_total * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    state_bytes = sum(8 * p.N for p in ps)
+    alg_bytes = 4 * total + state_bytes                  # per launch: outputs + state load/store
+    avg_launch = statistics.mean(launch_ms)
+    achieved = alg_bytes / (avg_launch * 1e-3) / 1e9
+    traffic = None
+    if os.path.exists(NCU_TRAFFIC):
+        with open(NCU_TRAFFIC) as f:
+            tr = json.load(f)
+        if tr.get("kernel_hash") == kernel_hash() and tr.get("workload") == args.workload:
+            traffic = tr.get("bytes_per_launch")
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        host = torch.empty(total, dtype=torch.int32, pin_memory=True)
+        pool.generate_host(reqs, host)                       # warm-up (allocates staging)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            pool.generate_host(reqs, host)
+        dt = time.perf_counter() - t0
+        e2e = {"value": total * args.e2e_steps / dt / 1e9, "unit": "Gnum/s",
+               "h2d_bytes_per_step": 64 * len(reqs), "d2h_bytes_per_step": 4 * total,
+               "steps": args.e2e_steps, "path": "mtgp_pool_generate_host into pinned host memory"}
+        del host
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        v, cores, dt, done = cpu_baseline(wl, args.cpu_numbers)
+        cpu = {"value": v, "unit": "Gnum/s", "cores": cores, "kind": "oracle",
+               "sample": f"all {len(wl.gens)} generator instances of {wl.name} x {args.cpu_numbers} numbers "
+                         f"({done:.3g} numbers, {dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gnum/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": {"c1": "C1: MTGP11213 x 1 generator x 2^20 u32",
+                                    "c2": "C2: MTGP11213, 128 sets x 2^24 x {u32, f[1,2), f[0,1)}, blocked",
+                                    "c3": "C3: MTGP23209 + MTGP44497, 128 sets each x 2^26 f[0,1)",
+                                    "c4": "C4: 8192 generators, mixed mexp, log-uniform 2^10..2^24, persistent",
+                                    "c2s": "C2 at 2^20 numbers per generator (profiling size)",
+                                    }[args.workload],
+                       "generators": len(wl.gens), "numbers_per_step": total,
+                       "bytes_written_per_step": 4 * total,
+                       "l2": "outputs larger than the 129 MB L2 every step; no flush",
+                       "launch": cfg, "parallelism": f"generator shards x{world}"},
+            "hbm_write_gbs": 4 * numbers_all / world / (ms_total * 1e-3) / 1e9,
+            "write_probe_gbs": write_probe_gbs,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_generate", "alg_bytes_per_launch": alg_bytes,
+                         "avg_launch_ms": avg_launch, "frac_of_write_probe": achieved / write_probe_gbs},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+            "kernel_hash": kernel_hash(),
+        }
+        print(json.dumps(line))
+    if sampler:
+        sampler.stop()
+    pool.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

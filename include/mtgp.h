@@ -1,0 +1,264 @@
+/*
+ * libmtgp -- MTGP generation on one GB300 GPU (sm_103a), C ABI.
+ *
+ * MTGP is the Mersenne Twister for Graphic Processors of Saito and Matsumoto
+ * ("Variants of Mersenne Twister Suitable for Graphic Processors", arXiv
+ * 1005.4973).  One generator's state of N = ceil(mexp / 32) 32-bit words is
+ * owned by one thread block, which computes many steps of the F2-linear
+ * recursion at once (Sec. 3.2), tempers them (Sec. 3.7) and writes uint32 or
+ * single-precision outputs (Sec. 6) to device memory.
+ *
+ * Conventions for every call:
+ *   - Functions return an mtgp_status and never abort; on failure
+ *     mtgp_last_error() returns a message for the calling thread.
+ *   - Pointers named dev_* are raw CUDA device pointers owned by the caller.
+ *     Pointers named host_* are host pointers owned by the caller.
+ *   - stream arguments are cudaStream_t values passed as void * (NULL is the
+ *     legacy default stream).  Calls are stream-ordered and asynchronous
+ *     unless stated otherwise; nothing synchronises implicitly.
+ *   - Objects (mtgp_state, mtgp_pool) are created and owned by the library;
+ *     the caller destroys them.  Their generator states stay resident in
+ *     device memory between calls, so generation continues where the last
+ *     call stopped (Sec. 8).
+ *   - A pool is used by at most one stream at a time: a call on a second
+ *     stream while work from the first is still in flight returns MTGP_EBUSY.
+ */
+#ifndef MTGP_H
+#define MTGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MTGP_MAX_N 4096u          /* largest state, in 32-bit words             */
+#define MTGP_PARAMS_VERSION 1u
+
+typedef enum mtgp_status {
+    MTGP_OK = 0,
+    MTGP_EINVAL = 1,     /* an argument is out of range or inconsistent        */
+    MTGP_ENOMEM = 2,     /* device or host allocation failed                    */
+    MTGP_ECUDA = 3,      /* a CUDA runtime call failed (message has the code)   */
+    MTGP_ETIMEOUT = 4,   /* a bounded device-side wait ran out                  */
+    MTGP_EBUSY = 5       /* the object has work in flight on another stream     */
+} mtgp_status;
+
+/* Output types (Sec. 6).  Every output occupies 4 bytes. */
+typedef enum mtgp_dtype {
+    MTGP_U32 = 0,        /* tempered 32-bit integer o_{N+i}                      */
+    MTGP_F32_12 = 1,     /* float in [1,2): 0x3F800000 | (o >> 9)                */
+    MTGP_F32_01 = 2      /* float in [0,1): the [1,2) float minus 1.0f (exact)  */
+} mtgp_dtype;
+
+typedef enum mtgp_layout {
+    MTGP_LAYOUT_BLOCKED = 0,      /* request j writes its n numbers contiguously
+                                     from element out_offset                      */
+    MTGP_LAYOUT_INTERLEAVED = 1   /* all requests have the same n; numbers go out
+                                     in chunks of `chunk` per request, round robin
+                                     over the requests in array order             */
+} mtgp_layout;
+
+/*
+ * One MTGP parameter set: the recursion parameters (N, M = pos, w = 32, r,
+ * sh1, sh2, R) of the Definition in Sec. 3.6 and the tempering parameter T of
+ * the Definition in Sec. 3.7, with R and T given as their 16-entry look-up
+ * tables: rec_tbl[b] = b R and tmp_tbl[b] = b T for the 4-bit row vector b
+ * (Sec. 3.6, 3.7).  N = ceil(mexp / 32), r = 32 N - mexp (Sec. 3.3),
+ * mask = BITMASK(32, r): the 32 - r MSBs set (Sec. 3.6).  `id` is the 32-bit
+ * generator ID of Sec. 5 (informational; it is embedded in R by the drawer).
+ * The single-precision table of Sec. 6 is derived from tmp_tbl.
+ */
+typedef struct mtgp_params {
+    uint32_t mexp, N, r, mask, pos, sh1, sh2, id;
+    uint32_t rec_tbl[16];
+    uint32_t tmp_tbl[16];
+} mtgp_params;
+
+typedef struct mtgp_state mtgp_state;   /* one device-resident generator       */
+typedef struct mtgp_pool mtgp_pool;     /* many device-resident generators     */
+
+/* One unit of batched work: n numbers of generator `gen` (an index into the
+ * pool, 0 .. count-1) of type dtype.  Requests naming the same generator in
+ * one call are applied in array order, each continuing the stream. */
+typedef struct mtgp_request {
+    uint32_t gen;
+    uint32_t dtype;          /* mtgp_dtype                                       */
+    uint64_t n;              /* numbers to generate; 0 is allowed (no-op)       */
+    uint64_t out_offset;     /* element offset into the output (blocked layout) */
+} mtgp_request;
+
+/* Launch configuration of a pool (chosen by mtgp_autotune or set by hand). */
+typedef struct mtgp_config {
+    uint32_t threads;          /* threads per block, multiple of 32, 32..1024       */
+    uint32_t words_per_round;  /* cap on words computed per round; the round size of
+                                  a generator is min(cap, N - M), rounded down to a
+                                  multiple of 32 when it is at least 32 (Sec. 3.2);
+                                  0 = no cap                                         */
+    uint32_t persistent;       /* 1: grid of SMs x blocks_per_sm blocks taking work
+                                  items longest first from a device counter;
+                                  0: one block per work item                        */
+    uint32_t blocks_per_sm;    /* persistent grid occupancy, 0 = what fits           */
+    uint32_t chunk;            /* interleaved layout chunk, power of two >= 32      */
+} mtgp_config;
+
+/* ---- library ------------------------------------------------------------ */
+
+/* Version string of the library. */
+const char *mtgp_version(void);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *mtgp_last_error(void);
+
+/* ---- parameter sets (host only, pure) ------------------------------------ */
+
+/*
+ * Draws a synthetic parameter set of exponent mexp with the structure that
+ * MTGPDC gives its sets (Sec. 5): ID[31:16] in the 16 MSBs of row 0 of R,
+ * ID[15:0] in MSB positions 13..28 of row 1, the LSB nibbles of the rows
+ * redrawn until the 4x4 block plus the identity is invertible, the rest of R
+ * and all of T random, sh1 = 13, sh2 = 4, M uniform in 2 < M < N - [N]_2
+ * (the Sec. 3.5 range M >= 2, N - M >= [N-2]_2 where that one is empty).
+ * Randomness: the SplitMix64 stream started at param_seed, drawn in the order
+ * M, rows of R, rejected LSB nibbles, rows of T.  Drawn sets are not searched
+ * for full period.  Errors: MTGP_EINVAL if mexp < 65 or N > MTGP_MAX_N or
+ * out is NULL.
+ */
+mtgp_status mtgp_params_draw(uint32_t mexp, uint64_t param_seed, uint32_t id, mtgp_params *out);
+
+/*
+ * Checks a parameter set: N, r and mask consistent with mexp (Sec. 3.3, 3.6),
+ * 2 <= pos < N, 1 <= sh1, sh2 <= 31, both tables F2-linear (tbl[a ^ b] =
+ * tbl[a] ^ tbl[b], so tbl[0] = 0), the LSB block of R invertible (Sec. 5), and
+ * N <= MTGP_MAX_N.  Returns MTGP_OK or MTGP_EINVAL with the reason.
+ */
+mtgp_status mtgp_params_validate(const mtgp_params *p);
+
+/* ---- single generator (Sec. 8 host/kernel flow) --------------------------- */
+
+/*
+ * Creates one generator with parameter set p, generator ID gen_id and 64-bit
+ * seed, and initialises its state in device memory on `stream` (the paper
+ * leaves seeding open; the state words are SplitMix64 outputs keyed by seed
+ * and gen_id, with the all-zero state excluded).  The library owns the state.
+ * Errors: MTGP_EINVAL (invalid p), MTGP_ENOMEM, MTGP_ECUDA.
+ */
+mtgp_status mtgp_state_create(const mtgp_params *p, uint32_t gen_id, uint64_t seed,
+                              void *stream, mtgp_state **out);
+
+/*
+ * Generates the next n numbers of the generator as dtype into dev_out
+ * (>= 4 n bytes, 4-byte aligned, caller-owned) and advances its state by n,
+ * stream-ordered on `stream`: one block loads the state into a shared-memory
+ * ring, runs rounds of the recursion (Sec. 3.2, 3.6), tempers (Sec. 3.7),
+ * converts (Sec. 6), stores, and writes the state back (Sec. 8).  n = 0 is a
+ * no-op.  Errors: MTGP_EINVAL (bad dtype, NULL dev_out with n > 0),
+ * MTGP_EBUSY, MTGP_ECUDA.
+ */
+mtgp_status mtgp_generate(mtgp_state *s, mtgp_dtype dt, void *dev_out, uint64_t n, void *stream);
+
+/*
+ * Checkpoint: copies the generator (parameters, stream position, state) to
+ * host_buf.  If host_buf is NULL, only *bytes is set to the size needed.
+ * Synchronises with the last stream the generator was used on.
+ */
+mtgp_status mtgp_state_save(const mtgp_state *s, void *host_buf, size_t *bytes);
+
+/* Restores a checkpoint made by mtgp_state_save (same N).  Synchronous. */
+mtgp_status mtgp_state_load(mtgp_state *s, const void *host_buf, size_t bytes);
+
+/* Numbers generated so far by the generator (its stream position). */
+mtgp_status mtgp_state_position(const mtgp_state *s, uint64_t *pos);
+
+/* Frees the generator (after synchronising with its last stream). */
+void mtgp_state_destroy(mtgp_state *s);
+
+/* ---- many generators: batched and served forms ---------------------------- */
+
+/*
+ * Creates `count` device-resident generators: generator i has parameter set
+ * ps[i], ID gen_ids[i] and seed seeds[i] (the same seeding as
+ * mtgp_state_create).  Parameter sets may mix exponents.  States are laid out
+ * back to back in one device buffer, each 16-byte aligned.
+ * Errors: MTGP_EINVAL, MTGP_ENOMEM, MTGP_ECUDA.
+ */
+mtgp_status mtgp_pool_create(const mtgp_params *ps, const uint32_t *gen_ids, const uint64_t *seeds,
+                             uint32_t count, void *stream, mtgp_pool **out);
+
+/* Number of generators and device bytes held by the pool. */
+mtgp_status mtgp_pool_info(const mtgp_pool *p, uint32_t *count, uint64_t *device_bytes);
+
+/* Reads / sets the pool's launch configuration (validated: MTGP_EINVAL). */
+mtgp_status mtgp_pool_get_config(const mtgp_pool *p, mtgp_config *cfg);
+mtgp_status mtgp_pool_set_config(mtgp_pool *p, const mtgp_config *cfg);
+
+/*
+ * Runs nreq requests in one kernel launch on `stream`.  Requests of the same
+ * generator are grouped, in array order, into one work item that one block
+ * runs start to finish (a generator's stream is sequential, Sec. 3.2); work
+ * items of different generators run in parallel blocks.  Blocked layout:
+ * request j writes elements [out_offset, out_offset + n) of dev_out.
+ * Interleaved layout: every request has the same n and a distinct generator,
+ * out_offset is ignored, and number k of request j goes to element
+ * (k / chunk) * (nreq * chunk) + j * chunk + k % chunk.
+ * dev_out must be 4-byte aligned (16-byte aligned for the fastest stores) and
+ * large enough; it is caller-owned.  Errors: MTGP_EINVAL (bad index, dtype or
+ * layout), MTGP_EBUSY, MTGP_ENOMEM, MTGP_ECUDA.
+ */
+mtgp_status mtgp_pool_generate(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
+                               void *dev_out, mtgp_layout layout, void *stream);
+
+/*
+ * End-to-end form of mtgp_pool_generate: the outputs land in HOST memory.
+ * Generation runs into library-owned device staging buffers of at most
+ * staging_bytes each (0 = 1 GiB) and each slice is copied to host_out while
+ * the next one is generated.  host_out should be pinned (cudaHostAlloc) for
+ * full copy bandwidth.  Returns after all copies completed (synchronous).
+ */
+mtgp_status mtgp_pool_generate_host(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
+                                    void *host_out, mtgp_layout layout, uint64_t staging_bytes,
+                                    void *stream);
+
+/* Stream position of generator i (numbers generated so far). Synchronous. */
+mtgp_status mtgp_pool_position(mtgp_pool *p, uint32_t i, uint64_t *pos);
+
+/*
+ * Copies generator i's state words (N of them, oldest first: x_k .. x_{k+N-1}
+ * after k numbers) to host_state.  Synchronous.  For tests and checkpoints.
+ */
+mtgp_status mtgp_pool_read_state(mtgp_pool *p, uint32_t i, uint32_t *host_state);
+
+/* Checkpoint of the whole pool: same contract as mtgp_state_save / _load. */
+mtgp_status mtgp_pool_save(mtgp_pool *p, void *host_buf, size_t *bytes);
+mtgp_status mtgp_pool_load(mtgp_pool *p, const void *host_buf, size_t bytes);
+
+/* Frees the pool (after synchronising with its last stream). */
+void mtgp_pool_destroy(mtgp_pool *p);
+
+/*
+ * Picks threads, words per round, persistent mode and occupancy
+ * for this pool by timing candidate configurations on `stream` with the given
+ * requests written to dev_scratch (caller-owned, large enough for them).  The
+ * generators' states are saved before and restored after, so tuning does not
+ * advance any stream.  On success the best configuration is set on the pool
+ * and copied to *best (if not NULL); *best_ms receives its time (if not NULL).
+ * Synchronous.
+ */
+mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_scratch,
+                          void *stream, mtgp_config *best, float *best_ms);
+
+/* ---- measurement helper --------------------------------------------------- */
+
+/*
+ * Write-only bandwidth probe: fills `words` 32-bit words of dev_buf with a
+ * pattern using 16-byte stores from a grid sized to the SM count; the
+ * achievable HBM write rate bounds every generation kernel here (each number
+ * costs 4 bytes written and nothing read).  Stream-ordered.
+ */
+mtgp_status mtgp_fill_probe(void *dev_buf, uint64_t words, uint32_t pattern, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MTGP_H */

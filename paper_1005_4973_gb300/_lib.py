@@ -1,0 +1,139 @@
+"""ctypes binding of libmtgp (include/mtgp.h): argument marshalling only.
+
+Every function keeps the C name; device buffers are passed as torch CUDA
+tensors (or raw integer addresses) and streams as torch.cuda.Stream objects
+(or raw cudaStream_t integers).  Nothing here computes any part of the
+generation path; if the shared library is missing, importing this module
+raises ImportError instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libmtgp.so")
+
+MTGP_OK, MTGP_EINVAL, MTGP_ENOMEM, MTGP_ECUDA, MTGP_ETIMEOUT, MTGP_EBUSY = range(6)
+MTGP_U32, MTGP_F32_12, MTGP_F32_01 = 0, 1, 2
+MTGP_LAYOUT_BLOCKED, MTGP_LAYOUT_INTERLEAVED = 0, 1
+MTGP_MAX_N = 4096
+STATUS_NAMES = {0: "MTGP_OK", 1: "MTGP_EINVAL", 2: "MTGP_ENOMEM", 3: "MTGP_ECUDA",
+                4: "MTGP_ETIMEOUT", 5: "MTGP_EBUSY"}
+
+
+class MTGPError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class mtgp_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("mexp", "N", "r", "mask", "pos", "sh1", "sh2", "id")] + [
+        ("rec_tbl", ctypes.c_uint32 * 16), ("tmp_tbl", ctypes.c_uint32 * 16)]
+
+
+class mtgp_request(ctypes.Structure):
+    _fields_ = [("gen", ctypes.c_uint32), ("dtype", ctypes.c_uint32),
+                ("n", ctypes.c_uint64), ("out_offset", ctypes.c_uint64)]
+
+
+class mtgp_config(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ("threads", "words_per_round", "persistent", "blocks_per_sm", "chunk")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_vp, _u32, _u64, _sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
+_P = ctypes.POINTER
+_SIGS = {
+    "mtgp_version": (ctypes.c_char_p, []),
+    "mtgp_last_error": (ctypes.c_char_p, []),
+    "mtgp_params_draw": (ctypes.c_int, [_u32, _u64, _u32, _P(mtgp_params)]),
+    "mtgp_params_validate": (ctypes.c_int, [_P(mtgp_params)]),
+    "mtgp_state_create": (ctypes.c_int, [_P(mtgp_params), _u32, _u64, _vp, _P(_vp)]),
+    "mtgp_generate": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _u64, _vp]),
+    "mtgp_state_save": (ctypes.c_int, [_vp, _vp, _P(_sz)]),
+    "mtgp_state_load": (ctypes.c_int, [_vp, _vp, _sz]),
+    "mtgp_state_position": (ctypes.c_int, [_vp, _P(_u64)]),
+    "mtgp_state_destroy": (None, [_vp]),
+    "mtgp_pool_create": (ctypes.c_int, [_P(mtgp_params), _P(_u32), _P(_u64), _u32, _vp, _P(_vp)]),
+    "mtgp_pool_info": (ctypes.c_int, [_vp, _P(_u32), _P(_u64)]),
+    "mtgp_pool_get_config": (ctypes.c_int, [_vp, _P(mtgp_config)]),
+    "mtgp_pool_set_config": (ctypes.c_int, [_vp, _P(mtgp_config)]),
+    "mtgp_pool_generate": (ctypes.c_int, [_vp, _P(mtgp_request), _u32, _vp, ctypes.c_int, _vp]),
+    "mtgp_pool_generate_host": (ctypes.c_int, [_vp, _P(mtgp_request), _u32, _vp, ctypes.c_int, _u64, _vp]),
+    "mtgp_pool_position": (ctypes.c_int, [_vp, _u32, _P(_u64)]),
+    "mtgp_pool_read_state": (ctypes.c_int, [_vp, _u32, _P(_u32)]),
+    "mtgp_pool_save": (ctypes.c_int, [_vp, _vp, _P(_sz)]),
+    "mtgp_pool_load": (ctypes.c_int, [_vp, _vp, _sz]),
+    "mtgp_pool_destroy": (None, [_vp]),
+    "mtgp_autotune": (ctypes.c_int, [_vp, _P(mtgp_request), _u32, _vp, _vp, _P(mtgp_config),
+                                     _P(ctypes.c_float)]),
+    "mtgp_fill_probe": (ctypes.c_int, [_vp, _u64, _u32, _vp]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmtgp is not built ({LIB_PATH} missing); run "
+                          f"`python -m paper_1005_4973_gb300.build` first -- there is no fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
+LIB = _load()
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def last_error() -> str:
+    return LIB.mtgp_last_error().decode()
+
+
+def check(status: int) -> None:
+    if status != MTGP_OK:
+        raise MTGPError(status, last_error())
+
+
+def ptr(x) -> int | None:
+    """Device or host address of a torch tensor, numpy array or int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def stream_handle(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def requests_array(reqs) -> ctypes.Array:
+    """List of (gen, dtype, n, out_offset) tuples or mtgp_request -> C array."""
+    arr = (mtgp_request * max(len(reqs), 1))()
+    for i, r in enumerate(reqs):
+        if isinstance(r, mtgp_request):
+            arr[i] = r
+        else:
+            arr[i] = mtgp_request(*[int(v) for v in r])
+    return arr

@@ -1,0 +1,829 @@
+// Host side of libmtgp: parameter sets, device-resident generator pools, work
+// lists and launches.  Implements the C ABI declared in include/mtgp.h.
+#include "mtgp.h"
+#include "mtgp_internal.h"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace mtgp;
+
+namespace {
+
+thread_local std::string g_err;
+
+mtgp_status fail(mtgp_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+mtgp_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(MTGP_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(MTGP_ECUDA, "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+}
+
+#define CU(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---- SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) -------------------------
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+uint64_t splitmix_next(uint64_t &s)
+{
+    s += kGamma;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+uint32_t pow2_floor(uint32_t x)
+{
+    uint32_t p = 1;
+    while (p <= x / 2u) p <<= 1;
+    return p;
+}
+
+uint32_t pow2_ceil(uint32_t x)
+{
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Table of a 4x32 matrix: entry b = (4-bit row vector b) x matrix, where the
+// leftmost component of b (its bit 3) multiplies row 0 (Sec. 3.6, 3.7, 5).
+void rows_to_table(const uint32_t rows[4], uint32_t tbl[16])
+{
+    for (uint32_t b = 0; b < 16u; ++b) {
+        uint32_t v = 0;
+        if (b & 8u) v ^= rows[0];
+        if (b & 4u) v ^= rows[1];
+        if (b & 2u) v ^= rows[2];
+        if (b & 1u) v ^= rows[3];
+        tbl[b] = v;
+    }
+}
+
+// v -> (v ^ rec[v]) restricted to the four LSBs is a bijection iff the 4x4
+// LSB block of R plus the identity is invertible (Sec. 5).
+bool lsb_block_bijective(const uint32_t rec[16])
+{
+    unsigned seen = 0;
+    for (uint32_t v = 0; v < 16u; ++v) seen |= 1u << ((v ^ rec[v]) & 15u);
+    return seen == 0xFFFFu;
+}
+
+bool table_linear(const uint32_t t[16])
+{
+    for (uint32_t a = 0; a < 16u; ++a)
+        for (uint32_t b = 0; b < 16u; ++b)
+            if (t[a ^ b] != (t[a] ^ t[b])) return false;
+    return true;
+}
+
+void mexp_derive(uint32_t mexp, uint32_t *N, uint32_t *r, uint32_t *mask)
+{
+    *N = (mexp + 31u) / 32u;
+    *r = 32u * *N - mexp;
+    *mask = *r >= 32u ? 0u : (0xFFFFFFFFu << *r);
+}
+
+// M range: Sec. 5 draws 2 < M < N - [N]_2; Sec. 3.5 (M >= 2, N - M >= [N-2]_2)
+// is used for states too small for that range.
+void pos_range(uint32_t N, uint32_t *lo, uint32_t *hi)
+{
+    const uint32_t f = pow2_floor(N);
+    if (N >= f + 4u) {
+        *lo = 3u;
+        *hi = N - f - 1u;
+    } else {
+        *lo = 2u;
+        *hi = N - pow2_floor(N - 2u);
+    }
+}
+
+struct Slice {        // piece of a request routed to a staging buffer
+    uint32_t gen, dtype;
+    uint64_t n, host_off;
+};
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// objects
+// --------------------------------------------------------------------------
+struct mtgp_pool {
+    uint32_t count = 0;
+    uint32_t max_N = 0;
+    int device = 0;
+    int sm_count = 0;
+    std::vector<DevGen> host_gens;         // parameters + offsets (count field stale)
+    DevGen *d_gens = nullptr;
+    uint32_t *d_state = nullptr;
+    uint64_t state_words = 0;
+    unsigned *d_ctl = nullptr;             // [0] work counter, [1] error flags
+    // work-list upload
+    void *h_stage = nullptr;               // pinned
+    size_t h_stage_bytes = 0;
+    void *d_work = nullptr;
+    size_t d_work_bytes = 0;
+    cudaEvent_t ev_upload = nullptr;       // upload out of h_stage done
+    bool upload_pending = false;
+    // in-flight tracking
+    cudaEvent_t ev_done = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool used = false;
+    // end-to-end staging
+    void *d_e2e[2] = {nullptr, nullptr};
+    size_t e2e_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_gen[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copy[2] = {nullptr, nullptr};
+    mtgp_config cfg{};
+};
+
+struct mtgp_state {
+    mtgp_pool *pool = nullptr;
+};
+
+namespace {
+
+const mtgp_config kDefaultConfig = {256u, 0u, 0u, 0u, 256u};
+
+mtgp_status check_config(const mtgp_config &c)
+{
+    if (c.threads < 32u || c.threads > 1024u || c.threads % 32u)
+        return fail(MTGP_EINVAL, "threads must be a multiple of 32 in [32, 1024], got %u", c.threads);
+    if (c.persistent > 1u) return fail(MTGP_EINVAL, "persistent must be 0 or 1");
+    if (c.blocks_per_sm > 32u) return fail(MTGP_EINVAL, "blocks_per_sm must be <= 32");
+    if (c.chunk < 32u || (c.chunk & (c.chunk - 1u)))
+        return fail(MTGP_EINVAL, "chunk must be a power of two >= 32, got %u", c.chunk);
+    return MTGP_OK;
+}
+
+// Waits until the pool's last work finished (for synchronous calls).
+mtgp_status pool_sync(mtgp_pool *p)
+{
+    if (p->used) CU(cudaEventSynchronize(p->ev_done), "cudaEventSynchronize");
+    if (p->upload_pending) {
+        CU(cudaEventSynchronize(p->ev_upload), "cudaEventSynchronize");
+        p->upload_pending = false;
+    }
+    return MTGP_OK;
+}
+
+mtgp_status pool_busy_check(mtgp_pool *p, cudaStream_t s)
+{
+    if (!p->used || s == p->last_stream) return MTGP_OK;
+    const cudaError_t e = cudaEventQuery(p->ev_done);
+    if (e == cudaErrorNotReady)
+        return fail(MTGP_EBUSY, "pool has work in flight on another stream");
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventQuery");
+    return MTGP_OK;
+}
+
+mtgp_status ensure_upload_space(mtgp_pool *p, size_t bytes)
+{
+    if (p->upload_pending) {
+        CU(cudaEventSynchronize(p->ev_upload), "cudaEventSynchronize");
+        p->upload_pending = false;
+    }
+    if (bytes > p->h_stage_bytes) {
+        if (p->h_stage) CU(cudaFreeHost(p->h_stage), "cudaFreeHost");
+        p->h_stage = nullptr;
+        const size_t nb = std::max(bytes, (size_t)1 << 16);
+        CU(cudaHostAlloc(&p->h_stage, nb, cudaHostAllocDefault), "cudaHostAlloc");
+        p->h_stage_bytes = nb;
+    }
+    if (bytes > p->d_work_bytes) {
+        if (p->used) CU(cudaEventSynchronize(p->ev_done), "cudaEventSynchronize");
+        if (p->d_work) CU(cudaFree(p->d_work), "cudaFree");
+        p->d_work = nullptr;
+        const size_t nb = std::max(bytes, (size_t)1 << 16);
+        CU(cudaMalloc(&p->d_work, nb), "cudaMalloc work list");
+        p->d_work_bytes = nb;
+    }
+    return MTGP_OK;
+}
+
+// Builds the work list of a request batch into the pool's upload buffers.
+struct Plan {
+    std::vector<DevWork> work;
+    std::vector<DevSeg> segs;
+    uint32_t wmax = 0;
+    uint32_t nmax = 0;
+    uint64_t total = 0;
+};
+
+mtgp_status build_plan(const mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, mtgp_layout layout,
+                       Plan *plan)
+{
+    if (nreq && !reqs) return fail(MTGP_EINVAL, "reqs is NULL");
+    if (layout != MTGP_LAYOUT_BLOCKED && layout != MTGP_LAYOUT_INTERLEAVED)
+        return fail(MTGP_EINVAL, "unknown layout %d", (int)layout);
+    const mtgp_config &c = p->cfg;
+    std::vector<int32_t> slot(p->count, -1);
+    std::vector<std::vector<DevSeg>> per;
+    std::vector<uint32_t> gens;
+    const uint32_t clog = (uint32_t)__builtin_ctz(c.chunk);
+    for (uint32_t j = 0; j < nreq; ++j) {
+        const mtgp_request &r = reqs[j];
+        if (r.gen >= p->count) return fail(MTGP_EINVAL, "request %u: generator %u out of range", j, r.gen);
+        if (r.dtype > 2u) return fail(MTGP_EINVAL, "request %u: unknown dtype %u", j, r.dtype);
+        if (layout == MTGP_LAYOUT_INTERLEAVED && r.n != reqs[0].n)
+            return fail(MTGP_EINVAL, "interleaved layout needs equal n in every request");
+        if (r.n == 0) continue;
+        DevSeg s{};
+        s.n = r.n;
+        s.dtype = r.dtype;
+        if (layout == MTGP_LAYOUT_BLOCKED) {
+            s.out_off = r.out_offset;
+            s.stride = 0;
+            s.chunk_log2 = kBlocked;
+        } else {
+            s.out_off = (uint64_t)j * c.chunk;
+            s.stride = (uint64_t)nreq * c.chunk;
+            s.chunk_log2 = clog;
+        }
+        if (slot[r.gen] < 0) {
+            slot[r.gen] = (int32_t)per.size();
+            per.emplace_back();
+            gens.push_back(r.gen);
+        } else if (layout == MTGP_LAYOUT_INTERLEAVED) {
+            return fail(MTGP_EINVAL, "interleaved layout needs distinct generators");
+        }
+        per[(size_t)slot[r.gen]].push_back(s);
+    }
+    plan->work.clear();
+    plan->segs.clear();
+    for (size_t w = 0; w < per.size(); ++w) {
+        DevWork dw{};
+        dw.gen = gens[w];
+        dw.seg_begin = (uint32_t)plan->segs.size();
+        dw.seg_count = (uint32_t)per[w].size();
+        for (const DevSeg &s : per[w]) {
+            dw.total += s.n;
+            plan->segs.push_back(s);
+        }
+        plan->total += dw.total;
+        const DevGen &g = p->host_gens[dw.gen];
+        plan->nmax = std::max(plan->nmax, g.N);
+        plan->work.push_back(dw);
+    }
+    if (c.persistent)   // longest first, so the tail of the persistent grid is short work
+        std::stable_sort(plan->work.begin(), plan->work.end(),
+                         [](const DevWork &a, const DevWork &b) { return a.total > b.total; });
+    return MTGP_OK;
+}
+
+mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStream_t s)
+{
+    if (plan.work.empty()) return MTGP_OK;
+    const mtgp_config &c = p->cfg;
+    // round size and ring
+    uint32_t wmax = 0, need = 0;
+    for (const DevWork &w : plan.work) {
+        const DevGen &g = p->host_gens[w.gen];
+        const uint32_t wg = round_words(g.N, g.M, c.words_per_round, c.threads, kMaxQ);
+        wmax = std::max(wmax, wg);
+    }
+    uint32_t qmax = 1;
+    while (qmax * c.threads < wmax && qmax < kMaxQ && c.threads <= max_threads_for_q(qmax * 2u)) qmax <<= 1;
+    for (const DevWork &w : plan.work) {
+        const DevGen &g = p->host_gens[w.gen];
+        need = std::max(need, g.N + round_words(g.N, g.M, c.words_per_round, c.threads, qmax));
+    }
+    const uint32_t ring = pow2_ceil(need);
+    // upload
+    const size_t wbytes = plan.work.size() * sizeof(DevWork);
+    const size_t sbytes = plan.segs.size() * sizeof(DevSeg);
+    mtgp_status st = ensure_upload_space(p, wbytes + sbytes);
+    if (st != MTGP_OK) return st;
+    std::memcpy(p->h_stage, plan.work.data(), wbytes);
+    std::memcpy((char *)p->h_stage + wbytes, plan.segs.data(), sbytes);
+    CU(cudaMemcpyAsync(p->d_work, p->h_stage, wbytes + sbytes, cudaMemcpyHostToDevice, s), "upload work list");
+    CU(cudaEventRecord(p->ev_upload, s), "cudaEventRecord");
+    p->upload_pending = true;
+    uint32_t grid = (uint32_t)plan.work.size();
+    if (c.persistent) {
+        CU(cudaMemsetAsync(p->d_ctl, 0, sizeof(unsigned), s), "reset work counter");
+        int occ = 0;
+        CU(generate_occupancy(c.threads, qmax, ring, &occ), "occupancy");
+        if (occ < 1) return fail(MTGP_EINVAL, "configuration does not fit on an SM");
+        const int per_sm = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, occ) : occ;
+        grid = std::min<uint32_t>(grid, (uint32_t)(per_sm * p->sm_count));
+    }
+    LaunchArgs a{};
+    a.gens = p->d_gens;
+    a.state = p->d_state;
+    a.work = (const DevWork *)p->d_work;
+    a.segs = (const DevSeg *)((char *)p->d_work + wbytes);
+    a.out = (uint32_t *)dev_out;
+    a.counter = p->d_ctl;
+    a.err = p->d_ctl + 1;
+    a.nwork = (uint32_t)plan.work.size();
+    a.ring_words = ring;
+    a.wpr_cap = c.words_per_round;
+    a.persistent = c.persistent;
+    CU(launch_generate(a, c.threads, grid, qmax, s), "generate kernel launch");
+    CU(cudaEventRecord(p->ev_done, s), "cudaEventRecord");
+    p->last_stream = s;
+    p->used = true;
+    return MTGP_OK;
+}
+
+mtgp_status pool_run(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_out,
+                     mtgp_layout layout, cudaStream_t s)
+{
+    mtgp_status st = pool_busy_check(p, s);
+    if (st != MTGP_OK) return st;
+    Plan plan;
+    st = build_plan(p, reqs, nreq, layout, &plan);
+    if (st != MTGP_OK) return st;
+    if (plan.total && !dev_out) return fail(MTGP_EINVAL, "dev_out is NULL");
+    if (((uintptr_t)dev_out & 3u) != 0) return fail(MTGP_EINVAL, "dev_out must be 4-byte aligned");
+    return launch_plan(p, plan, dev_out, s);
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// C ABI
+// --------------------------------------------------------------------------
+extern "C" {
+
+const char *mtgp_version(void) { return "libmtgp 0.1 (sm_103a)"; }
+
+const char *mtgp_last_error(void) { return g_err.c_str(); }
+
+mtgp_status mtgp_params_draw(uint32_t mexp, uint64_t param_seed, uint32_t id, mtgp_params *out)
+{
+    if (!out) return fail(MTGP_EINVAL, "out is NULL");
+    if (mexp < 65u) return fail(MTGP_EINVAL, "mexp %u too small (N must be >= 3)", mexp);
+    mtgp_params p{};
+    mexp_derive(mexp, &p.N, &p.r, &p.mask);
+    if (p.N > MTGP_MAX_N) return fail(MTGP_EINVAL, "mexp %u gives N = %u > %u", mexp, p.N, MTGP_MAX_N);
+    uint32_t lo, hi;
+    pos_range(p.N, &lo, &hi);
+    uint64_t s = param_seed;
+    p.mexp = mexp;
+    p.id = id;
+    p.pos = lo + (uint32_t)(splitmix_next(s) % (uint64_t)(hi - lo + 1u));
+    uint32_t R[4], T[4];
+    for (uint32_t &row : R) row = (uint32_t)splitmix_next(s);
+    R[0] = (R[0] & 0x0000FFFFu) | (id & 0xFFFF0000u);               // ID[31:16]
+    R[1] = (R[1] & ~0x000FFFF0u) | ((id & 0x0000FFFFu) << 4);        // ID[15:0]
+    for (;;) {
+        rows_to_table(R, p.rec_tbl);
+        if (lsb_block_bijective(p.rec_tbl)) break;
+        for (uint32_t &row : R) row = (row & ~0xFu) | ((uint32_t)splitmix_next(s) & 0xFu);
+    }
+    for (uint32_t &row : T) row = (uint32_t)splitmix_next(s);
+    rows_to_table(T, p.tmp_tbl);
+    p.sh1 = 13u;
+    p.sh2 = 4u;
+    *out = p;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_params_validate(const mtgp_params *p)
+{
+    if (!p) return fail(MTGP_EINVAL, "params is NULL");
+    if (p->mexp < 65u) return fail(MTGP_EINVAL, "mexp %u too small", p->mexp);
+    uint32_t N, r, mask;
+    mexp_derive(p->mexp, &N, &r, &mask);
+    if (p->N != N || p->r != r || p->mask != mask)
+        return fail(MTGP_EINVAL, "N/r/mask (%u/%u/%08x) inconsistent with mexp %u", p->N, p->r, p->mask, p->mexp);
+    if (N > MTGP_MAX_N) return fail(MTGP_EINVAL, "N = %u exceeds %u", N, MTGP_MAX_N);
+    if (p->pos < 2u || p->pos >= N) return fail(MTGP_EINVAL, "pos %u outside [2, N)", p->pos);
+    if (p->sh1 < 1u || p->sh1 > 31u || p->sh2 < 1u || p->sh2 > 31u)
+        return fail(MTGP_EINVAL, "shifts must be in [1, 31]");
+    if (!table_linear(p->rec_tbl) || !table_linear(p->tmp_tbl))
+        return fail(MTGP_EINVAL, "look-up tables are not F2-linear");
+    if (!lsb_block_bijective(p->rec_tbl))
+        return fail(MTGP_EINVAL, "LSB block of R plus identity is singular");
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_create(const mtgp_params *ps, const uint32_t *gen_ids, const uint64_t *seeds,
+                             uint32_t count, void *stream, mtgp_pool **out)
+{
+    if (!out) return fail(MTGP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ps || !gen_ids || !seeds || count == 0) return fail(MTGP_EINVAL, "empty or NULL pool arguments");
+    for (uint32_t i = 0; i < count; ++i) {
+        mtgp_status st = mtgp_params_validate(&ps[i]);
+        if (st != MTGP_OK) {
+            std::string m = g_err;
+            return fail(st, "parameter set %u: %s", i, m.c_str());
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    mtgp_pool *p = new (std::nothrow) mtgp_pool;
+    if (!p) return fail(MTGP_ENOMEM, "host allocation");
+    p->count = count;
+    p->cfg = kDefaultConfig;
+    p->host_gens.resize(count);
+    uint64_t off = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        DevGen &g = p->host_gens[i];
+        std::memset(&g, 0, sizeof g);
+        g.N = ps[i].N;
+        g.M = ps[i].pos;
+        g.mask = ps[i].mask;
+        g.sh1 = ps[i].sh1;
+        g.sh2 = ps[i].sh2;
+        g.mexp = ps[i].mexp;
+        g.id = ps[i].id;
+        g.state_off = off;
+        std::memcpy(g.rec, ps[i].rec_tbl, sizeof g.rec);
+        std::memcpy(g.tmp, ps[i].tmp_tbl, sizeof g.tmp);
+        off += (g.N + 3u) & ~3u;                   // 16-byte aligned states
+        p->max_N = std::max(p->max_N, g.N);
+    }
+    p->state_words = off;
+    auto cleanup = [&](mtgp_status st) { mtgp_pool_destroy(p); return st; };
+    cudaError_t e;
+#define CUP(call, what)                                           \
+    do {                                                          \
+        e = (call);                                               \
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, what)); \
+    } while (0)
+    CUP(cudaGetDevice(&p->device), "cudaGetDevice");
+    CUP(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device), "SM count");
+    CUP(cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming), "cudaEventCreate");
+    CUP(cudaEventCreateWithFlags(&p->ev_upload, cudaEventDisableTiming), "cudaEventCreate");
+    CUP(cudaMalloc(&p->d_gens, sizeof(DevGen) * count), "cudaMalloc generators");
+    CUP(cudaMalloc(&p->d_state, sizeof(uint32_t) * off), "cudaMalloc states");
+    CUP(cudaMalloc(&p->d_ctl, 4 * sizeof(unsigned)), "cudaMalloc control");
+    CUP(cudaMemsetAsync(p->d_ctl, 0, 4 * sizeof(unsigned), s), "cudaMemsetAsync");
+    // upload parameters and seeding inputs through one pinned staging buffer
+    const size_t gbytes = sizeof(DevGen) * count, ibytes = sizeof(uint32_t) * count,
+                 sbytes = sizeof(uint64_t) * count;
+    const size_t ioff = gbytes, soff = (gbytes + ibytes + 15u) & ~(size_t)15u;
+    mtgp_status st = ensure_upload_space(p, soff + sbytes);
+    if (st != MTGP_OK) return cleanup(st);
+    std::memcpy(p->h_stage, p->host_gens.data(), gbytes);
+    std::memcpy((char *)p->h_stage + ioff, gen_ids, ibytes);
+    std::memcpy((char *)p->h_stage + soff, seeds, sbytes);
+    CUP(cudaMemcpyAsync(p->d_gens, p->h_stage, gbytes, cudaMemcpyHostToDevice, s), "upload generators");
+    CUP(cudaMemcpyAsync(p->d_work, (char *)p->h_stage + ioff, soff + sbytes - ioff, cudaMemcpyHostToDevice, s),
+        "upload seeds");
+    CUP(launch_seed(p->d_gens, p->d_state, (const uint32_t *)p->d_work,
+                    (const uint64_t *)((char *)p->d_work + (soff - ioff)), 0, count, s),
+        "seed kernel launch");
+    CUP(cudaEventRecord(p->ev_upload, s), "cudaEventRecord");
+    p->upload_pending = true;
+    CUP(cudaEventRecord(p->ev_done, s), "cudaEventRecord");
+    p->last_stream = s;
+    p->used = true;
+#undef CUP
+    *out = p;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_info(const mtgp_pool *p, uint32_t *count, uint64_t *device_bytes)
+{
+    if (!p) return fail(MTGP_EINVAL, "pool is NULL");
+    if (count) *count = p->count;
+    if (device_bytes)
+        *device_bytes = sizeof(DevGen) * (uint64_t)p->count + 4ull * p->state_words + p->d_work_bytes +
+                        2ull * p->e2e_bytes;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_get_config(const mtgp_pool *p, mtgp_config *cfg)
+{
+    if (!p || !cfg) return fail(MTGP_EINVAL, "NULL argument");
+    *cfg = p->cfg;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_set_config(mtgp_pool *p, const mtgp_config *cfg)
+{
+    if (!p || !cfg) return fail(MTGP_EINVAL, "NULL argument");
+    mtgp_status st = check_config(*cfg);
+    if (st != MTGP_OK) return st;
+    p->cfg = *cfg;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_generate(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_out,
+                               mtgp_layout layout, void *stream)
+{
+    if (!p) return fail(MTGP_EINVAL, "pool is NULL");
+    return pool_run(p, reqs, nreq, dev_out, layout, (cudaStream_t)stream);
+}
+
+mtgp_status mtgp_pool_generate_host(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *host_out,
+                                    mtgp_layout layout, uint64_t staging_bytes, void *stream)
+{
+    if (!p) return fail(MTGP_EINVAL, "pool is NULL");
+    if (layout != MTGP_LAYOUT_BLOCKED) return fail(MTGP_EINVAL, "host output supports the blocked layout only");
+    if (nreq && !reqs) return fail(MTGP_EINVAL, "reqs is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    mtgp_status st = pool_busy_check(p, s);
+    if (st != MTGP_OK) return st;
+    uint64_t total = 0;
+    for (uint32_t j = 0; j < nreq; ++j) {
+        if (reqs[j].gen >= p->count || reqs[j].dtype > 2u) return fail(MTGP_EINVAL, "request %u invalid", j);
+        total += reqs[j].n;
+    }
+    if (!total) return MTGP_OK;
+    if (!host_out) return fail(MTGP_EINVAL, "host_out is NULL");
+    if (!staging_bytes) staging_bytes = 1ull << 30;
+    staging_bytes &= ~15ull;
+    if (staging_bytes < 4096u) return fail(MTGP_EINVAL, "staging_bytes too small");
+    if (staging_bytes > p->e2e_bytes) {
+        st = pool_sync(p);
+        if (st != MTGP_OK) return st;
+        for (int b = 0; b < 2; ++b) {
+            if (p->d_e2e[b]) CU(cudaFree(p->d_e2e[b]), "cudaFree");
+            p->d_e2e[b] = nullptr;
+        }
+        p->e2e_bytes = 0;
+        for (int b = 0; b < 2; ++b) CU(cudaMalloc(&p->d_e2e[b], staging_bytes), "cudaMalloc staging");
+        p->e2e_bytes = staging_bytes;
+    }
+    if (!p->copy_stream) {
+        CU(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (int b = 0; b < 2; ++b) {
+            CU(cudaEventCreateWithFlags(&p->ev_gen[b], cudaEventDisableTiming), "cudaEventCreate");
+            CU(cudaEventCreateWithFlags(&p->ev_copy[b], cudaEventDisableTiming), "cudaEventCreate");
+            CU(cudaEventRecord(p->ev_copy[b], p->copy_stream), "cudaEventRecord");
+        }
+    }
+    const uint64_t cap = p->e2e_bytes / 4u;
+    std::vector<Slice> slices;
+    std::vector<mtgp_request> batch;
+    int buf = 0;
+    auto flush = [&]() -> mtgp_status {
+        if (slices.empty()) return MTGP_OK;
+        CU(cudaStreamWaitEvent(s, p->ev_copy[buf], 0), "cudaStreamWaitEvent");
+        batch.clear();
+        uint64_t off = 0;
+        for (const Slice &sl : slices) {
+            batch.push_back(mtgp_request{sl.gen, sl.dtype, sl.n, off});
+            off += sl.n;
+        }
+        mtgp_status r = pool_run(p, batch.data(), (uint32_t)batch.size(), p->d_e2e[buf], MTGP_LAYOUT_BLOCKED, s);
+        if (r != MTGP_OK) return r;
+        CU(cudaEventRecord(p->ev_gen[buf], s), "cudaEventRecord");
+        CU(cudaStreamWaitEvent(p->copy_stream, p->ev_gen[buf], 0), "cudaStreamWaitEvent");
+        off = 0;
+        for (const Slice &sl : slices) {
+            CU(cudaMemcpyAsync((char *)host_out + 4u * sl.host_off, (char *)p->d_e2e[buf] + 4u * off, 4u * sl.n,
+                               cudaMemcpyDeviceToHost, p->copy_stream),
+               "copy to host");
+            off += sl.n;
+        }
+        CU(cudaEventRecord(p->ev_copy[buf], p->copy_stream), "cudaEventRecord");
+        slices.clear();
+        buf ^= 1;
+        return MTGP_OK;
+    };
+    uint64_t used = 0;
+    for (uint32_t j = 0; j < nreq; ++j) {
+        uint64_t left = reqs[j].n, host_off = reqs[j].out_offset;
+        while (left) {
+            if (used == cap) {
+                st = flush();
+                if (st != MTGP_OK) return st;
+                used = 0;
+            }
+            const uint64_t take = std::min(left, cap - used);
+            slices.push_back(Slice{reqs[j].gen, reqs[j].dtype, take, host_off});
+            used += take;
+            left -= take;
+            host_off += take;
+        }
+    }
+    st = flush();
+    if (st != MTGP_OK) return st;
+    CU(cudaStreamSynchronize(p->copy_stream), "cudaStreamSynchronize");
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_position(mtgp_pool *p, uint32_t i, uint64_t *pos)
+{
+    if (!p || !pos || i >= p->count) return fail(MTGP_EINVAL, "bad pool, index or NULL pos");
+    mtgp_status st = pool_sync(p);
+    if (st != MTGP_OK) return st;
+    CU(cudaMemcpy(pos, (const char *)p->d_gens + sizeof(DevGen) * i + offsetof(DevGen, count), sizeof(uint64_t),
+                  cudaMemcpyDeviceToHost),
+       "read position");
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_read_state(mtgp_pool *p, uint32_t i, uint32_t *host_state)
+{
+    if (!p || !host_state || i >= p->count) return fail(MTGP_EINVAL, "bad pool, index or NULL buffer");
+    mtgp_status st = pool_sync(p);
+    if (st != MTGP_OK) return st;
+    const DevGen &g = p->host_gens[i];
+    CU(cudaMemcpy(host_state, p->d_state + g.state_off, 4u * g.N, cudaMemcpyDeviceToHost), "read state");
+    return MTGP_OK;
+}
+
+// Checkpoint format: "MTGP" magic, version, count, state_words, then the
+// DevGen records, then the state buffer.
+mtgp_status mtgp_pool_save(mtgp_pool *p, void *host_buf, size_t *bytes)
+{
+    if (!p || !bytes) return fail(MTGP_EINVAL, "NULL argument");
+    const size_t need = 16u + sizeof(DevGen) * p->count + 4u * p->state_words;
+    if (!host_buf) {
+        *bytes = need;
+        return MTGP_OK;
+    }
+    if (*bytes < need) return fail(MTGP_EINVAL, "buffer of %zu bytes, need %zu", *bytes, need);
+    mtgp_status st = pool_sync(p);
+    if (st != MTGP_OK) return st;
+    uint32_t hdr[4] = {0x5047544Du, MTGP_PARAMS_VERSION, p->count, (uint32_t)p->state_words};
+    std::memcpy(host_buf, hdr, 16);
+    CU(cudaMemcpy((char *)host_buf + 16, p->d_gens, sizeof(DevGen) * p->count, cudaMemcpyDeviceToHost),
+       "save generators");
+    CU(cudaMemcpy((char *)host_buf + 16 + sizeof(DevGen) * p->count, p->d_state, 4u * p->state_words,
+                  cudaMemcpyDeviceToHost),
+       "save states");
+    *bytes = need;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_load(mtgp_pool *p, const void *host_buf, size_t bytes)
+{
+    if (!p || !host_buf) return fail(MTGP_EINVAL, "NULL argument");
+    const size_t need = 16u + sizeof(DevGen) * p->count + 4u * p->state_words;
+    if (bytes != need) return fail(MTGP_EINVAL, "checkpoint of %zu bytes, expected %zu", bytes, need);
+    uint32_t hdr[4];
+    std::memcpy(hdr, host_buf, 16);
+    if (hdr[0] != 0x5047544Du || hdr[1] != MTGP_PARAMS_VERSION || hdr[2] != p->count ||
+        hdr[3] != (uint32_t)p->state_words)
+        return fail(MTGP_EINVAL, "checkpoint header does not match this pool");
+    const DevGen *gs = (const DevGen *)((const char *)host_buf + 16);
+    for (uint32_t i = 0; i < p->count; ++i) {
+        DevGen a = gs[i], b = p->host_gens[i];
+        a.count = b.count = 0;
+        if (std::memcmp(&a, &b, sizeof a) != 0)
+            return fail(MTGP_EINVAL, "checkpoint generator %u has other parameters", i);
+    }
+    mtgp_status st = pool_sync(p);
+    if (st != MTGP_OK) return st;
+    CU(cudaMemcpy(p->d_gens, gs, sizeof(DevGen) * p->count, cudaMemcpyHostToDevice), "load generators");
+    CU(cudaMemcpy(p->d_state, (const char *)host_buf + 16 + sizeof(DevGen) * p->count, 4u * p->state_words,
+                  cudaMemcpyHostToDevice),
+       "load states");
+    return MTGP_OK;
+}
+
+void mtgp_pool_destroy(mtgp_pool *p)
+{
+    if (!p) return;
+    if (p->used && p->ev_done) cudaEventSynchronize(p->ev_done);
+    if (p->copy_stream) cudaStreamSynchronize(p->copy_stream);
+    if (p->upload_pending && p->ev_upload) cudaEventSynchronize(p->ev_upload);
+    cudaFree(p->d_gens);
+    cudaFree(p->d_state);
+    cudaFree(p->d_ctl);
+    cudaFree(p->d_work);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(p->d_e2e[b]);
+        if (p->ev_gen[b]) cudaEventDestroy(p->ev_gen[b]);
+        if (p->ev_copy[b]) cudaEventDestroy(p->ev_copy[b]);
+    }
+    if (p->h_stage) cudaFreeHost(p->h_stage);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    if (p->ev_done) cudaEventDestroy(p->ev_done);
+    if (p->ev_upload) cudaEventDestroy(p->ev_upload);
+    delete p;
+}
+
+// ---- single generator: a pool of one ---------------------------------------
+mtgp_status mtgp_state_create(const mtgp_params *params, uint32_t gen_id, uint64_t seed, void *stream,
+                              mtgp_state **out)
+{
+    if (!out) return fail(MTGP_EINVAL, "out is NULL");
+    *out = nullptr;
+    mtgp_state *s = new (std::nothrow) mtgp_state;
+    if (!s) return fail(MTGP_ENOMEM, "host allocation");
+    mtgp_status st = mtgp_pool_create(params, &gen_id, &seed, 1u, stream, &s->pool);
+    if (st != MTGP_OK) {
+        delete s;
+        return st;
+    }
+    *out = s;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_generate(mtgp_state *s, mtgp_dtype dt, void *dev_out, uint64_t n, void *stream)
+{
+    if (!s) return fail(MTGP_EINVAL, "state is NULL");
+    if ((uint32_t)dt > 2u) return fail(MTGP_EINVAL, "unknown dtype %d", (int)dt);
+    mtgp_request r{0u, (uint32_t)dt, n, 0u};
+    return pool_run(s->pool, &r, 1u, dev_out, MTGP_LAYOUT_BLOCKED, (cudaStream_t)stream);
+}
+
+mtgp_status mtgp_state_save(const mtgp_state *s, void *host_buf, size_t *bytes)
+{
+    if (!s) return fail(MTGP_EINVAL, "state is NULL");
+    return mtgp_pool_save(s->pool, host_buf, bytes);
+}
+
+mtgp_status mtgp_state_load(mtgp_state *s, const void *host_buf, size_t bytes)
+{
+    if (!s) return fail(MTGP_EINVAL, "state is NULL");
+    return mtgp_pool_load(s->pool, host_buf, bytes);
+}
+
+mtgp_status mtgp_state_position(const mtgp_state *s, uint64_t *pos)
+{
+    if (!s) return fail(MTGP_EINVAL, "state is NULL");
+    return mtgp_pool_position(s->pool, 0u, pos);
+}
+
+void mtgp_state_destroy(mtgp_state *s)
+{
+    if (!s) return;
+    mtgp_pool_destroy(s->pool);
+    delete s;
+}
+
+mtgp_status mtgp_fill_probe(void *dev_buf, uint64_t words, uint32_t pattern, void *stream)
+{
+    if (!dev_buf || ((uintptr_t)dev_buf & 15u) || (words & 3u))
+        return fail(MTGP_EINVAL, "fill probe needs a 16-byte aligned buffer and a multiple of 4 words");
+    CU(launch_fill((uint32_t *)dev_buf, words, pattern, (cudaStream_t)stream), "fill kernel launch");
+    return MTGP_OK;
+}
+
+// ---- autotuner ---------------------------------------------------------------
+mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_scratch, void *stream,
+                          mtgp_config *best, float *best_ms)
+{
+    if (!p) return fail(MTGP_EINVAL, "pool is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    mtgp_status st = pool_busy_check(p, s);
+    if (st != MTGP_OK) return st;
+    size_t bytes = 0;
+    st = mtgp_pool_save(p, nullptr, &bytes);
+    if (st != MTGP_OK) return st;
+    std::vector<char> ckpt(bytes);
+    st = mtgp_pool_save(p, ckpt.data(), &bytes);
+    if (st != MTGP_OK) return st;
+    const mtgp_config orig = p->cfg;
+    std::vector<mtgp_config> cands;
+    for (uint32_t threads : {128u, 256u, 512u, 1024u})
+        for (uint32_t wpr : {0u, 256u, 512u, 1024u})
+            for (uint32_t pers : {0u, 1u})
+                for (uint32_t bps : {0u, 1u, 2u, 3u}) {
+                    if (!pers && bps) continue;
+                    if (wpr && wpr < threads) continue;
+                    cands.push_back(mtgp_config{threads, wpr, pers, bps, orig.chunk});
+                }
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0), "cudaEventCreate");
+    CU(cudaEventCreate(&e1), "cudaEventCreate");
+    float best_t = 1e30f;
+    mtgp_config best_c = orig;
+    for (const mtgp_config &c : cands) {
+        p->cfg = c;
+        mtgp_status r = pool_run(p, reqs, nreq, dev_scratch, MTGP_LAYOUT_BLOCKED, s);   // warm-up
+        if (r != MTGP_OK) continue;
+        CU(cudaEventRecord(e0, s), "cudaEventRecord");
+        r = pool_run(p, reqs, nreq, dev_scratch, MTGP_LAYOUT_BLOCKED, s);
+        CU(cudaEventRecord(e1, s), "cudaEventRecord");
+        CU(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        if (r == MTGP_OK && ms < best_t) {
+            best_t = ms;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->cfg = best_c;
+    st = mtgp_pool_load(p, ckpt.data(), bytes);
+    if (st != MTGP_OK) return st;
+    if (best) *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    return MTGP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+"""Python face of libmtgp.  Same names as the C ABI (include/mtgp.h), plus two
+small owner classes (Pool, State) that free their handles.  Marshalling only:
+every number is produced by the CUDA kernels behind the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import (MTGP_F32_01, MTGP_F32_12, MTGP_LAYOUT_BLOCKED, MTGP_LAYOUT_INTERLEAVED,  # noqa: F401
+                   MTGP_MAX_N, MTGP_U32, MTGPError, mtgp_config, mtgp_params, mtgp_request)
+
+
+def mtgp_version() -> str:
+    return L.LIB.mtgp_version().decode()
+
+
+def mtgp_params_draw(mexp: int, param_seed: int, gen_id: int) -> mtgp_params:
+    p = mtgp_params()
+    L.check(L.LIB.mtgp_params_draw(mexp, param_seed, gen_id, ctypes.byref(p)))
+    return p
+
+
+def mtgp_params_validate(p: mtgp_params) -> None:
+    L.check(L.LIB.mtgp_params_validate(ctypes.byref(p)))
+
+
+def mtgp_fill_probe(dev_buf, words: int, pattern: int = 0x9E3779B9, stream=None) -> None:
+    L.check(L.LIB.mtgp_fill_probe(L.ptr(dev_buf), words, pattern, L.stream_handle(stream)))
+
+
+class Pool:
+    """Device-resident generators (mtgp_pool_*)."""
+
+    def __init__(self, params, gen_ids, seeds, stream=None):
+        params = list(params)
+        n = len(params)
+        parr = (mtgp_params * n)(*params)
+        ids = (ctypes.c_uint32 * n)(*[int(i) for i in gen_ids])
+        sds = (ctypes.c_uint64 * n)(*[int(s) for s in seeds])
+        h = ctypes.c_void_p()
+        L.check(L.LIB.mtgp_pool_create(parr, ids, sds, n, L.stream_handle(stream), ctypes.byref(h)))
+        self.handle = h
+        self.params = params
+        self.count = n
+
+    # -- generation ---------------------------------------------------------
+    def generate(self, reqs, out, layout=MTGP_LAYOUT_BLOCKED, stream=None) -> None:
+        arr = L.requests_array(reqs)
+        L.check(L.LIB.mtgp_pool_generate(self.handle, arr, len(reqs), L.ptr(out), layout,
+                                         L.stream_handle(stream)))
+
+    def generate_host(self, reqs, host_out, layout=MTGP_LAYOUT_BLOCKED, staging_bytes=0, stream=None) -> None:
+        arr = L.requests_array(reqs)
+        L.check(L.LIB.mtgp_pool_generate_host(self.handle, arr, len(reqs), L.ptr(host_out), layout,
+                                              staging_bytes, L.stream_handle(stream)))
+
+    # -- configuration ------------------------------------------------------
+    @property
+    def config(self) -> mtgp_config:
+        c = mtgp_config()
+        L.check(L.LIB.mtgp_pool_get_config(self.handle, ctypes.byref(c)))
+        return c
+
+    def set_config(self, **kw) -> mtgp_config:
+        c = self.config
+        for k, v in kw.items():
+            setattr(c, k, int(v))
+        L.check(L.LIB.mtgp_pool_set_config(self.handle, ctypes.byref(c)))
+        return c
+
+    def autotune(self, reqs, scratch, stream=None):
+        arr = L.requests_array(reqs)
+        best, ms = mtgp_config(), ctypes.c_float()
+        L.check(L.LIB.mtgp_autotune(self.handle, arr, len(reqs), L.ptr(scratch), L.stream_handle(stream),
+                                    ctypes.byref(best), ctypes.byref(ms)))
+        return best, ms.value
+
+    # -- state --------------------------------------------------------------
+    def position(self, i: int) -> int:
+        v = ctypes.c_uint64()
+        L.check(L.LIB.mtgp_pool_position(self.handle, i, ctypes.byref(v)))
+        return v.value
+
+    def read_state(self, i: int) -> np.ndarray:
+        st = np.zeros(self.params[i].N, dtype=np.uint32)
+        L.check(L.LIB.mtgp_pool_read_state(self.handle, i, st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+        return st
+
+    def save(self) -> bytes:
+        n = ctypes.c_size_t()
+        L.check(L.LIB.mtgp_pool_save(self.handle, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        L.check(L.LIB.mtgp_pool_save(self.handle, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def load(self, blob: bytes) -> None:
+        L.check(L.LIB.mtgp_pool_load(self.handle, blob, len(blob)))
+
+    def info(self):
+        c, b = ctypes.c_uint32(), ctypes.c_uint64()
+        L.check(L.LIB.mtgp_pool_info(self.handle, ctypes.byref(c), ctypes.byref(b)))
+        return c.value, b.value
+
+    def close(self) -> None:
+        if self.handle:
+            L.LIB.mtgp_pool_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class State:
+    """One device-resident generator (mtgp_state_*)."""
+
+    def __init__(self, params: mtgp_params, gen_id: int, seed: int, stream=None):
+        h = ctypes.c_void_p()
+        L.check(L.LIB.mtgp_state_create(ctypes.byref(params), gen_id, seed, L.stream_handle(stream),
+                                        ctypes.byref(h)))
+        self.handle = h
+        self.params = params
+
+    def generate(self, dtype: int, out, n: int, stream=None) -> None:
+        L.check(L.LIB.mtgp_generate(self.handle, dtype, L.ptr(out), n, L.stream_handle(stream)))
+
+    def position(self) -> int:
+        v = ctypes.c_uint64()
+        L.check(L.LIB.mtgp_state_position(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def save(self) -> bytes:
+        n = ctypes.c_size_t()
+        L.check(L.LIB.mtgp_state_save(self.handle, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        L.check(L.LIB.mtgp_state_save(self.handle, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def load(self, blob: bytes) -> None:
+        L.check(L.LIB.mtgp_state_load(self.handle, blob, len(blob)))
+
+    def close(self) -> None:
+        if self.handle:
+            L.LIB.mtgp_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,358 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every output is an exact integer or float bit pattern, so every comparison is
+bit-exact (the method's arithmetic is integer; the one float subtraction of
+Sec. 6 is exact).  Small cases compare everything; full-size cases compare
+sampled generators in full, every generator's prefix, every final state where
+the oracle can afford it, and closed-form relations between dtypes.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1005_4973_gb300 import workloads as WL
+from tests.helpers import as_u32, lib_pool, oracle_params, oracle_state, oracle_stream
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1005_4973_gb300 import build
+    build.build()
+    O.build()
+    assert torch.cuda.is_available()
+
+
+def _run(gens, reqs, layout=0, config=None, total=None):
+    pool = lib_pool(gens)
+    if config:
+        pool.set_config(**config)
+    if total is None:
+        total = sum(r[2] for r in reqs) if layout == 0 else len(reqs) * (reqs[0][2] if reqs else 0)
+    out = torch.full((max(total, 1),), 0xA5, dtype=torch.int32, device="cuda")
+    pool.generate(reqs, out, layout=layout)
+    torch.cuda.synchronize()
+    return pool, as_u32(out)[:total]
+
+
+def _check_blocked(gens, reqs, out, pool=None):
+    by_gen = {}
+    for g, dt, n, off in reqs:
+        by_gen.setdefault(g, []).append((dt, n, off))
+    for g, segs in by_gen.items():
+        outs, st = oracle_stream(gens[g], [(dt, n) for dt, n, _ in segs])
+        for (dt, n, off), ref in zip(segs, outs):
+            assert np.array_equal(out[off:off + n], ref), (gens[g], dt, n)
+        if pool is not None:
+            assert np.array_equal(pool.read_state(g), st), gens[g]
+            assert pool.position(g) == sum(n for _, n, _ in segs)
+
+
+# ---------------------------------------------------------------- seeding
+def test_seed_state_matches_oracle():
+    gens = [WL.GenSpec(m, s, s * 7 + 1, gid, seed) for m in (89, 11213, 23209, 44497)
+            for s, gid, seed in ((1, 0, 1234), (2, 5, 0), (3, 2**31, 2**63 + 17))]
+    pool = lib_pool(gens)
+    for i, g in enumerate(gens):
+        _, st = oracle_state(g)
+        assert np.array_equal(pool.read_state(i), st), g
+        assert pool.position(i) == 0
+
+
+# ------------------------------------------------------------------- C1
+@pytest.mark.parametrize("dtype", [WL.U32, WL.F12, WL.F01])
+def test_c1_full_size_bitexact(dtype):
+    wl = WL.c1(dtype=dtype)
+    pool, out = _run(wl.gens, wl.requests)
+    _check_blocked(wl.gens, wl.requests, out, pool)
+
+
+# -------------------------------------------------- launch-shape sweep
+MIXED = [WL.GenSpec(11213, 1, 0, 0), WL.GenSpec(23209, 2, 1, 1), WL.GenSpec(44497, 3, 2, 2),
+         WL.GenSpec(521, 4, 3, 3), WL.GenSpec(89, 5, 4, 4), WL.GenSpec(1279, 6, 5, 5),
+         WL.GenSpec(11213, 7, 0xFFFF0001, 6, 99)]
+RAGGED = [1, 31, 33, 255, 257, 1000, 4097, 12345]
+
+
+@pytest.mark.parametrize("threads", [32, 64, 96, 128, 256, 512, 1024])
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_launch_shapes(threads, persistent):
+    reqs, off = [], 0
+    for g in range(len(MIXED)):
+        for k, n in enumerate(RAGGED[g % 3::3] + [RAGGED[(g + 1) % len(RAGGED)]]):
+            reqs.append((g, (g + k) % 3, n, off))
+            off += n
+    pool, out = _run(MIXED, reqs, config=dict(threads=threads, persistent=persistent))
+    _check_blocked(MIXED, reqs, out, pool)
+
+
+@pytest.mark.parametrize("wpr", [1, 7, 32, 33, 64, 100, 256, 300, 1000])
+def test_round_size_caps(wpr):
+    reqs, off = [], 0
+    for g in range(len(MIXED)):
+        reqs.append((g, WL.U32, 5003, off))
+        off += 5003
+    pool, out = _run(MIXED, reqs, config=dict(threads=128, words_per_round=wpr))
+    _check_blocked(MIXED, reqs, out, pool)
+
+
+def test_random_shift_sets():
+    # sh1, sh2 over [1, 31] exercise every shift path; the shift values are
+    # recipe inputs (numpy RNG) applied to each side's own drawn set.
+    import paper_1005_4973_gb300 as M
+    rng = np.random.default_rng(5)
+    shifts = rng.integers(1, 32, size=(8, 2))
+    ps, ops = [], []
+    for s in range(8):
+        mexp = 11213 if s % 2 else 23209
+        lp = M.mtgp_params_draw(mexp, 100 + s, s)
+        lp.sh1, lp.sh2 = int(shifts[s, 0]), int(shifts[s, 1])
+        M.mtgp_params_validate(lp)
+        o = O.params_draw(mexp, 100 + s, s)
+        ops.append(O.params_from_fields(mexp, o.pos, int(shifts[s, 0]), int(shifts[s, 1]), s, list(o.R), list(o.T)))
+        ps.append(lp)
+    pool = M.Pool(ps, list(range(8)), [7] * 8)
+    reqs = [(i, i % 3, 7777, i * 7777) for i in range(8)]
+    out = torch.zeros(8 * 7777, dtype=torch.int32, device="cuda")
+    pool.generate(reqs, out)
+    torch.cuda.synchronize()
+    o = as_u32(out)
+    for i, op in enumerate(ops):
+        st = O.seed_state(op, i, 7)
+        assert np.array_equal(o[i * 7777:(i + 1) * 7777], O.generate(op, st, 7777, i % 3)), shifts[i]
+
+
+# ------------------------------------------------------------ edge cases
+def test_zero_length_and_empty():
+    pool = lib_pool(MIXED[:2])
+    out = torch.zeros(4, dtype=torch.int32, device="cuda")
+    pool.generate([], out)
+    pool.generate([(0, 0, 0, 0), (1, 2, 0, 0)], out)
+    torch.cuda.synchronize()
+    assert pool.position(0) == 0 and pool.position(1) == 0
+    assert not out.any()
+
+
+@pytest.mark.parametrize("splits", [(1, 1, 1), (255, 257, 31), (351, 352), (1000, 1, 4097), (65536, 3)])
+def test_continuation_across_calls(splits):
+    g = WL.GenSpec(11213, 9, 9, 9)
+    pool = lib_pool([g])
+    parts = []
+    for k, n in enumerate(splits):
+        out = torch.zeros(n, dtype=torch.int32, device="cuda")
+        pool.generate([(0, k % 3, n, 0)], out)
+        parts.append(as_u32(out))
+    outs, st = oracle_stream(g, [(k % 3, n) for k, n in enumerate(splits)])
+    for a, b in zip(parts, outs):
+        assert np.array_equal(a, b)
+    assert np.array_equal(pool.read_state(0), st)
+
+
+def test_same_generator_many_requests_in_one_call():
+    g = [WL.GenSpec(23209, 4, 4, 4), WL.GenSpec(11213, 5, 5, 5)]
+    reqs = [(0, 0, 100, 0), (1, 1, 50, 100), (0, 2, 3000, 150), (0, 1, 1, 3150), (1, 0, 999, 3151)]
+    pool, out = _run(g, reqs)
+    _check_blocked(g, reqs, out, pool)
+
+
+@pytest.mark.parametrize("chunk", [32, 256, 4096])
+def test_interleaved_layout(chunk):
+    gens = [WL.GenSpec(11213 if i % 2 else 44497, i + 1, i, i) for i in range(5)]
+    n = 3 * chunk + 17
+    reqs = [(i, i % 3, n, 0) for i in range(5)]
+    pool = lib_pool(gens)
+    pool.set_config(chunk=chunk)
+    total = 5 * n + 5 * chunk
+    out = torch.zeros(total, dtype=torch.int32, device="cuda")
+    pool.generate(reqs, out, layout=1)
+    torch.cuda.synchronize()
+    o = as_u32(out)
+    for j, g in enumerate(gens):
+        (ref,), _ = oracle_stream(g, [(j % 3, n)])
+        k = np.arange(n)
+        idx = (k // chunk) * (5 * chunk) + j * chunk + k % chunk
+        assert np.array_equal(o[idx], ref)
+
+
+def test_bad_requests_rejected():
+    import paper_1005_4973_gb300 as M
+    pool = lib_pool(MIXED[:2])
+    out = torch.zeros(16, dtype=torch.int32, device="cuda")
+    for reqs, layout in (([(2, 0, 4, 0)], 0), ([(0, 3, 4, 0)], 0), ([(0, 0, 4, 0), (1, 0, 5, 0)], 1),
+                         ([(0, 0, 4, 0), (0, 0, 4, 0)], 1)):
+        with pytest.raises(M.MTGPError):
+            pool.generate(reqs, out, layout=layout)
+    with pytest.raises(M.MTGPError):
+        pool.set_config(threads=48)
+    with pytest.raises(M.MTGPError):
+        pool.set_config(chunk=100)
+
+
+# ------------------------------------------------------ checkpoint / e2e
+def test_checkpoint_save_load():
+    gens = MIXED[:3]
+    pool = lib_pool(gens)
+    out = torch.zeros(3 * 5000, dtype=torch.int32, device="cuda")
+    pool.generate([(i, 0, 5000, 5000 * i) for i in range(3)], out)
+    blob = pool.save()
+    pool.generate([(i, 1, 5000, 5000 * i) for i in range(3)], out)
+    first = as_u32(out).copy()
+    pool.load(blob)
+    pool.generate([(i, 1, 5000, 5000 * i) for i in range(3)], out)
+    assert np.array_equal(as_u32(out), first)
+    for i, g in enumerate(gens):
+        outs, st = oracle_stream(g, [(0, 5000), (1, 5000)])
+        assert np.array_equal(first[5000 * i:5000 * (i + 1)], outs[1])
+        assert pool.position(i) == 10000
+
+
+def test_state_object_and_checkpoint():
+    import paper_1005_4973_gb300 as M
+    g = WL.GenSpec(11213, 1, 0, 0)
+    s = M.State(M.mtgp_params_draw(g.mexp, g.param_seed, g.id), g.gen_id, g.seed)
+    out = torch.zeros(70000, dtype=torch.int32, device="cuda")
+    s.generate(0, out, 30000)
+    blob = s.save()
+    s.generate(2, out[30000:], 40000)
+    torch.cuda.synchronize()
+    full = as_u32(out).copy()
+    assert s.position() == 70000
+    outs, _ = oracle_stream(g, [(0, 30000), (2, 40000)])
+    assert np.array_equal(full, np.concatenate(outs))
+    s.load(blob)
+    s.generate(2, out, 40000)
+    assert np.array_equal(as_u32(out)[:40000], outs[1])
+
+
+def test_generate_host_end_to_end():
+    gens = MIXED[:4]
+    reqs = [(0, 0, 300000, 0), (1, 2, 123457, 300000), (2, 1, 5, 423457), (3, 0, 77777, 423462)]
+    pool = lib_pool(gens)
+    host = torch.zeros(501239, dtype=torch.int32).pin_memory()
+    pool.generate_host(reqs, host, staging_bytes=1 << 18)      # forces many slices
+    o = host.numpy().view(np.uint32)
+    _check_blocked(gens, reqs, o, pool)
+
+
+# ------------------------------------------- reduced exponents, full period
+def test_full_period_sets_on_gpu():
+    import paper_1005_4973_gb300 as M
+    with open(os.path.join(GOLDEN, "full_period_sets.json")) as f:
+        sets = json.load(f)["sets"]
+    ps, ops = [], []
+    for d in sets:
+        ops.append(O.params_from_fields(d["mexp"], d["pos"], d["sh1"], d["sh2"], d["id"], d["R"], d["T"]))
+        ps.append(M.mtgp_params_draw(d["mexp"], d["param_seed"], d["id"]))
+    pool = M.Pool(ps, list(range(len(ps))), [3] * len(ps))
+    n = 20011
+    out = torch.zeros(n * len(ps), dtype=torch.int32, device="cuda")
+    pool.generate([(i, i % 3, n, i * n) for i in range(len(ps))], out)
+    o = as_u32(out)
+    for i, op in enumerate(ops):
+        st = O.seed_state(op, i, 3)
+        assert np.array_equal(o[i * n:(i + 1) * n], O.generate(op, st, n, i % 3)), sets[i]["mexp"]
+
+
+# ----------------------------------------------------- full-size configs
+def _oracle_final_states(gens, n, dtype, nthreads=None):
+    """Oracle streams of many generators in chunks; returns final states and
+    the first `keep` outputs of each."""
+    keep = 1 << 16
+    states, heads = [], []
+    batch = 8
+    for b in range(0, len(gens), batch):
+        ps, sts = [], []
+        for g in gens[b:b + batch]:
+            p, st = oracle_state(g)
+            ps.append(p)
+            sts.append(st)
+        outs = O.generate_many(ps, sts, [n] * len(ps), [dtype] * len(ps), nthreads)
+        states += sts
+        heads += [o[:keep].copy() for o in outs]
+        del outs
+    return states, heads
+
+
+def test_c2_full_size():
+    """C2: 128 sets x 2^24 x {u32, f12, f01}, the bench's launch (one block per
+    generator instance, 384 instances in one launch)."""
+    wl = WL.c2()
+    n = 1 << 24
+    pool = lib_pool(wl.gens)
+    out = torch.empty(wl.total_numbers, dtype=torch.int32, device="cuda")
+    pool.generate(wl.requests, out)
+    torch.cuda.synchronize()
+    u = out[: 128 * n].view(128, n)
+    f12 = out[128 * n: 256 * n].view(128, n)
+    f01 = out[256 * n:].view(128, n)
+    # Sec. 6 closed forms relate the three runs of each set at full size
+    assert torch.equal(f12, (u >> 9) & 0x7FFFFF | 0x3F800000)
+    ff = f12.view(torch.float32) - 1.0
+    assert torch.equal(f01.view(torch.float32), ff)
+    # every generator's final state and first 2^16 numbers against the oracle (uint32 run)
+    states, heads = _oracle_final_states(wl.gens[:128], n, WL.U32)
+    uh = as_u32(u[:, : 1 << 16])
+    for i in range(128):
+        assert np.array_equal(uh[i], heads[i]), i
+        assert np.array_equal(pool.read_state(i), states[i]), i
+        assert np.array_equal(pool.read_state(256 + i), states[i]), i
+    # two generators compared in full
+    for i in (0, 127):
+        (ref,), _ = oracle_stream(wl.gens[i], [(WL.U32, n)])
+        assert np.array_equal(as_u32(u[i]), ref)
+
+
+@pytest.mark.parametrize("mexp", [23209, 44497])
+def test_c3_full_size(mexp):
+    wl = WL.c3(mexps=(mexp,))
+    n = 1 << 26
+    pool = lib_pool(wl.gens)
+    out = torch.empty(wl.total_numbers, dtype=torch.int32, device="cuda")
+    pool.generate(wl.requests, out)
+    torch.cuda.synchronize()
+    f = out.view(128, n)
+    fv = f.view(torch.float32)
+    assert float(fv.min()) >= 0.0 and float(fv.max()) < 1.0
+    # f01 * 2^23 is an exact integer < 2^23
+    assert torch.equal(torch.floor(fv * 8388608.0), fv * 8388608.0)
+    heads_ref = []
+    for i in range(128):
+        p, st = oracle_state(wl.gens[i])
+        heads_ref.append(O.generate(p, st, 1 << 14, WL.F01))
+    fh = as_u32(f[:, : 1 << 14])
+    for i in range(128):
+        assert np.array_equal(fh[i], heads_ref[i]), i
+    for i in (5, 100):
+        (ref,), st = oracle_stream(wl.gens[i], [(WL.F01, n)])
+        assert np.array_equal(as_u32(f[i]), ref)
+        assert np.array_equal(pool.read_state(i), st)
+
+
+def test_c4_batched_sampled():
+    """C4: 8192 generators, mixed exponents, log-uniform lengths, in the
+    persistent longest-first launch; sampled generators in full, all prefixes."""
+    wl = WL.c4()
+    pool = lib_pool(wl.gens)
+    pool.set_config(persistent=1)
+    out = torch.empty(wl.total_numbers, dtype=torch.int32, device="cuda")
+    pool.generate(wl.requests, out)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    sample = sorted(set(rng.integers(0, 8192, 24).tolist()) | {int(np.argmax([r[2] for r in wl.requests]))})
+    for g in sample:
+        _, dt, n, off = wl.requests[g]
+        (ref,), st = oracle_stream(wl.gens[g], [(dt, n)])
+        assert np.array_equal(as_u32(out[off:off + n]), ref), g
+        assert np.array_equal(pool.read_state(g), st), g
+    for g in range(0, 8192, 16):
+        _, dt, n, off = wl.requests[g]
+        k = min(n, 1024)
+        p, st = oracle_state(wl.gens[g])
+        assert np.array_equal(as_u32(out[off:off + k]), O.generate(p, st, k, dt)), g

@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MTGP Gnum/s & HBM write GB/s vs peak (plain vs batched); served p50/p99 latency"
-KERNEL_SOURCES = ["paper_1005_4973_gb300/csrc/mtgp_kernels.cu", "paper_1005_4973_gb300/csrc/mtgp_internal.h"]
+KERNEL_SOURCES = ["paper_1005_4973_gb300/csrc/mtgp_device.cuh", "paper_1005_4973_gb300/csrc/mtgp_internal.h"]
 NCU_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -194,7 +194,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-numbers", type=int, default=1 << 22, help="numbers per generator in the CPU sample")
     ap.add_argument("--ref-numbers", type=int, default=1 << 16, help="numbers per generator per reference step")
-    ap.add_argument("--config", default="", help="JSON launch config overrides (threads, words_per_round, ...)")
+    ap.add_argument("--config", default="", help="JSON launch config overrides (threads, slots, persistent, ...)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -89,18 +89,20 @@ typedef struct mtgp_request {
     uint64_t out_offset;     /* element offset into the output (blocked layout) */
 } mtgp_request;
 
-/* Launch configuration of a pool (chosen by mtgp_autotune or set by hand). */
+/* Launch configuration of a pool (chosen by mtgp_autotune or set by hand).
+ * A generator runs in rounds of S = N - M words (Sec. 3.2); each thread of a
+ * block owns ceil(S / threads) of the S columns, at most 11 (32 threads),
+ * 12 (64), 11 (128), 6 (256) or 8 (512). */
 typedef struct mtgp_config {
-    uint32_t threads;          /* threads per block, multiple of 32, 32..1024       */
-    uint32_t words_per_round;  /* cap on words computed per round; the round size of
-                                  a generator is min(cap, N - M), rounded down to a
-                                  multiple of 32 when it is at least 32 (Sec. 3.2);
-                                  0 = no cap                                         */
+    uint32_t threads;          /* threads per block: 32, 64, 128, 256 or 512          */
     uint32_t persistent;       /* 1: grid of SMs x blocks_per_sm blocks taking work
                                   items longest first from a device counter;
-                                  0: one block per work item                        */
-    uint32_t blocks_per_sm;    /* persistent grid occupancy, 0 = what fits           */
-    uint32_t chunk;            /* interleaved layout chunk, power of two >= 32      */
+                                  0: one block per work item                         */
+    uint32_t blocks_per_sm;    /* persistent grid occupancy, 0 = what fits            */
+    uint32_t chunk;            /* interleaved layout chunk, power of two >= 32       */
+    uint32_t buffer_words;     /* shared-memory words per block, 0 = sized from the
+                                  launch (>= 2N + threads ceil(S / threads) + 32
+                                  is required)                                        */
 } mtgp_config;
 
 /* ---- library ------------------------------------------------------------ */
@@ -237,7 +239,7 @@ mtgp_status mtgp_pool_load(mtgp_pool *p, const void *host_buf, size_t bytes);
 void mtgp_pool_destroy(mtgp_pool *p);
 
 /*
- * Picks threads, words per round, persistent mode and occupancy
+ * Picks threads, persistent mode and occupancy
  * for this pool by timing candidate configurations on `stream` with the given
  * requests written to dev_scratch (caller-owned, large enough for them).  The
  * generators' states are saved before and restored after, so tuning does not

@@ -18,6 +18,9 @@ MTGP_OK, MTGP_EINVAL, MTGP_ENOMEM, MTGP_ECUDA, MTGP_ETIMEOUT, MTGP_EBUSY = range
 MTGP_U32, MTGP_F32_12, MTGP_F32_01 = 0, 1, 2
 MTGP_LAYOUT_BLOCKED, MTGP_LAYOUT_INTERLEAVED = 0, 1
 MTGP_MAX_N = 4096
+# block sizes compiled into the library and the column slots per thread each
+# supports (mirrors max_slots in the CUDA sources)
+MAX_SLOTS = {32: 11, 64: 12, 128: 11, 256: 6, 512: 8}
 STATUS_NAMES = {0: "MTGP_OK", 1: "MTGP_EINVAL", 2: "MTGP_ENOMEM", 3: "MTGP_ECUDA",
                 4: "MTGP_ETIMEOUT", 5: "MTGP_EBUSY"}
 
@@ -40,7 +43,7 @@ class mtgp_request(ctypes.Structure):
 
 class mtgp_config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
-                ("threads", "words_per_round", "persistent", "blocks_per_sm", "chunk")]
+                ("threads", "persistent", "blocks_per_sm", "chunk", "buffer_words")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

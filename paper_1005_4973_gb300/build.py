@@ -18,7 +18,8 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libmtgp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
-SOURCES = ["mtgp_kernels.cu", "mtgp_host.cpp"]
+SOURCES = ["mtgp_kernels.cu", "mtgp_gen_t32.cu", "mtgp_gen_t64.cu", "mtgp_gen_t128.cu", "mtgp_gen_t256.cu",
+           "mtgp_gen_t512.cu", "mtgp_host.cpp"]
 
 
 def _inputs():

@@ -1,0 +1,301 @@
+// Device code of the MTGP generation kernel, included by the per-block-size
+// translation units mtgp_gen_t*.cu (each instantiates k_generate<T, QMAX>).
+//
+// One thread block owns one generator at a time (Sec. 3.2).  The block keeps
+// the generator's recent words in a linear shared-memory buffer X, holding
+// x_j at X[j - off], and computes the sequence in rounds of S = N - M words:
+// round r produces x_{N+rS+c} for columns c = 0 .. S-1, all independent
+// because each reads only x_{rS+c}, x_{rS+c+1} and x_{rS+c+M} (Sec. 3.2).  A
+// round needs one block barrier.  When the next round would run past the end
+// of X, the N live words are copied back to the front (every ~30 rounds).
+//
+// Column c is owned by the same thread in every round, so the word
+// x_{rS+c+M} = x_{N+(r-1)S+c} that the recursion needs is that thread's own
+// output of the previous round and stays in a register; only x_{rS+c},
+// x_{rS+c+1} (recursion) and x_{rS+c+M-1} (tempering, Sec. 3.7) are read from
+// shared memory, at pointer + immediate addresses.
+//
+// The 16-entry tables are held one entry per lane and read with a width-16
+// warp shuffle, which takes the index modulo 16 in hardware.  Floats are
+// filled from the tempered integer o: 0x3F800000 | (o >> 9) is bit for bit
+// the paper's (x >> 9) ^ sngltbl[...] of Sec. 6 eq. C, since
+// sngltbl = 0x3F800000 | (tmptbl >> 9); [0,1) subtracts 1.0f (exact).
+#pragma once
+
+#include "mtgp_internal.h"
+
+namespace mtgp {
+namespace dev {
+
+// Output value of dtype dt from the tempered 32-bit integer o (Sec. 3.7, 6).
+__device__ __forceinline__ uint32_t finish(uint32_t dt, uint32_t o)
+{
+    const uint32_t f12 = 0x3F800000u | (o >> 9);
+    if (dt == 0u) return o;
+    if (dt == 1u) return f12;
+    return __float_as_uint(__fsub_rn(__uint_as_float(f12), 1.0f));
+}
+
+// Parameters of the generator a block is running.
+struct GenCtx {
+    uint32_t N, M, mask, sh1, sh2, S;
+    uint32_t rec_r, tmp_r;      // this lane's table entries rec[lane & 15], tmp[lane & 15]
+};
+
+// Block-wide barrier between rounds; a one-warp block only needs the warp's.
+template <int T>
+__device__ __forceinline__ void round_sync()
+{
+    if (T == 32)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
+// A full round of S words whose outputs all belong to one blocked segment of
+// dtype DT.  x points at this thread's x_{rS+tid}, out at its output slot.
+// Q = ceil(S / T): slots 0 .. Q-2 are full for every thread; slot Q-1 holds
+// the last S - (Q-1) T columns, and warps with none of them skip it.  The
+// full slots are processed stage by stage so their dependency chains
+// interleave.
+template <int T, int Q, int DT>
+__device__ __forceinline__ void round_fast(const GenCtx &g, uint32_t *x, uint32_t (&prev)[Q],
+                                           uint32_t *__restrict__ out, bool tail_warp, bool tail_lane)
+{
+    constexpr int F = Q - 1;                  // full slots
+    const uint32_t *xt_p = x + (g.M - 1u);
+    uint32_t *xn_p = x + g.N;
+    uint32_t a[Q], b[Q], c[Q], u[Q];
+#pragma unroll
+    for (int q = 0; q < F; ++q) {             // shared loads: x_i, x_{i+1}, x_{M-1+i}
+        a[q] = x[q * T];
+        b[q] = x[q * T + 1];
+        c[q] = xt_p[q * T];
+    }
+#pragma unroll
+    for (int q = 0; q < F; ++q) {             // recursion up to the table look-up (Sec. 3.6)
+        const uint32_t t = b[q] ^ (a[q] & g.mask);
+        u[q] = t ^ (t << g.sh1) ^ (prev[q] >> g.sh2);
+    }
+#pragma unroll
+    for (int q = 0; q < F; ++q)
+        b[q] = __shfl_sync(0xffffffffu, g.rec_r, (int)u[q], 16);
+#pragma unroll
+    for (int q = 0; q < F; ++q) {             // tempering index from x_{M-1+i} (Sec. 3.7)
+        uint32_t s = c[q] ^ (c[q] >> 16);
+        s ^= s >> 8;
+        c[q] = __shfl_sync(0xffffffffu, g.tmp_r, (int)s, 16);
+    }
+#pragma unroll
+    for (int q = 0; q < F; ++q) {
+        const uint32_t xn = u[q] ^ b[q];
+        xn_p[q * T] = xn;
+        prev[q] = xn;
+        __stcs(out + q * T, finish(DT, xn ^ c[q]));
+    }
+    if (tail_warp) {
+        constexpr int q = F;
+        const uint32_t a0 = x[q * T], b0 = x[q * T + 1], c0 = xt_p[q * T];
+        const uint32_t t = b0 ^ (a0 & g.mask);
+        const uint32_t uu = t ^ (t << g.sh1) ^ (prev[q] >> g.sh2);
+        const uint32_t xn = uu ^ __shfl_sync(0xffffffffu, g.rec_r, (int)uu, 16);
+        uint32_t s = c0 ^ (c0 >> 16);
+        s ^= s >> 8;
+        const uint32_t v = __shfl_sync(0xffffffffu, g.tmp_r, (int)s, 16);
+        if (tail_lane) {
+            xn_p[q * T] = xn;
+            prev[q] = xn;
+            __stcs(out + q * T, finish(DT, xn ^ v));
+        }
+    }
+}
+
+// Runs `rounds` full rounds inside one blocked segment of dtype DT.
+template <int T, int Q, int DT>
+__device__ __forceinline__ void run_fast(const GenCtx &g, uint32_t *buf, uint32_t B, uint32_t &rel,
+                                         uint32_t (&prev)[Q], uint32_t rounds, uint32_t *out)
+{
+    const uint32_t tid = threadIdx.x;
+    const bool tail_warp = (uint32_t)(Q - 1) * T + (tid & ~31u) < g.S;
+    const bool tail_lane = (uint32_t)(Q - 1) * T + tid < g.S;
+    out += tid;
+    for (uint32_t r = 0; r < rounds; ++r) {
+        if (rel + g.N + (uint32_t)(Q * T) + 32u > B) {      // compaction: live words to the front
+            for (uint32_t j = tid; j < g.N; j += T) buf[j] = buf[rel + j];
+            round_sync<T>();
+            rel = 0;
+        }
+        round_fast<T, Q, DT>(g, buf + rel + tid, prev, out, tail_warp, tail_lane);
+        round_sync<T>();
+        rel += g.S;
+        out += g.S;
+    }
+}
+
+// One word of the recursion (Sec. 3.6) from x0 = x_i, x1 = x_{i+1}, xm = x_{M+i},
+// and its tempered output (Sec. 3.7) from xt = x_{M-1+i}.
+__device__ __forceinline__ void step(const GenCtx &g, uint32_t x0, uint32_t x1, uint32_t xm,
+                                     uint32_t xt, uint32_t &xn, uint32_t &o)
+{
+    const uint32_t t = x1 ^ (x0 & g.mask);
+    const uint32_t u = t ^ (t << g.sh1) ^ (xm >> g.sh2);
+    xn = u ^ __shfl_sync(0xffffffffu, g.rec_r, (int)u, 16);
+    uint32_t s = xt ^ (xt >> 16);
+    s ^= s >> 8;
+    o = xn ^ __shfl_sync(0xffffffffu, g.tmp_r, (int)s, 16);
+}
+
+// A round that may be partial (S_r < S words) or span several segments of
+// any layout and dtype: each output finds its segment on its own.
+template <int T, int Q>
+__device__ __forceinline__ void round_general(const GenCtx &g, uint32_t *x, uint32_t (&prev)[Q],
+                                              uint32_t S_r, uint64_t k0, const DevSeg *segs,
+                                              uint32_t si, uint64_t seg_start, uint32_t *out)
+{
+    const uint32_t tid = threadIdx.x, wbase = tid & ~31u;
+    const uint32_t *xt_p = x + (g.M - 1u);
+    uint32_t *xn_p = x + g.N;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if (q * T + wbase < S_r) {
+            const uint32_t a = x[q * T], b = x[q * T + 1], c = xt_p[q * T];
+            uint32_t xn, o;
+            step(g, a, b, prev[q], c, xn, o);
+            if (q * T + tid < S_r) {
+                xn_p[q * T] = xn;
+                prev[q] = xn;
+                const uint64_t k = k0 + q * T + tid;
+                uint32_t s = si;
+                uint64_t start = seg_start, end = seg_start + segs[si].n;
+                while (k >= end) {
+                    ++s;
+                    start = end;
+                    end += segs[s].n;
+                }
+                const DevSeg sg = segs[s];
+                const uint64_t kk = k - start;
+                const uint64_t idx = sg.chunk_log2 == kBlocked
+                                         ? kk
+                                         : (kk >> sg.chunk_log2) * sg.stride + (kk & ((1ull << sg.chunk_log2) - 1ull));
+                __stcs(out + sg.out_off + idx, finish(sg.dtype, o));
+            }
+        }
+    }
+}
+
+// Moves the N live words x_{rS} .. x_{rS+N-1} to the front of the buffer when
+// the next round would run past its end (the caller guarantees rel >= N then,
+// so source and destination never overlap).
+template <int T, int Q>
+__device__ __forceinline__ void maybe_compact(const GenCtx &g, uint32_t *buf, uint32_t B, uint32_t &rel)
+{
+    if (rel + g.N + (uint32_t)(Q * T) + 32u > B) {
+        for (uint32_t j = threadIdx.x; j < g.N; j += T) buf[j] = buf[rel + j];
+        round_sync<T>();
+        rel = 0;
+    }
+}
+
+// All rounds of one work item (a generator's consecutive segments), with
+// Q = ceil(S / T) column slots per thread.
+template <int T, int Q>
+__device__ __forceinline__ void run_item(const GenCtx g, uint32_t *buf, uint32_t B, const DevWork w,
+                                      const DevSeg *segs, uint32_t *out_base, uint32_t *st)
+{
+    const uint32_t tid = threadIdx.x;
+    uint32_t prev[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)                          // x_{c+M}, c = column
+        prev[q] = (q * T + tid < g.S) ? buf[q * T + tid + g.M] : 0u;
+    uint32_t rel = 0, si = 0;
+    uint64_t k0 = 0, seg_start = 0, seg_end = segs[0].n;
+    while (k0 < w.total) {
+        while (k0 >= seg_end) {                          // skip finished segments
+            ++si;
+            seg_start = seg_end;
+            seg_end += segs[si].n;
+        }
+        const DevSeg sg = segs[si];
+        const uint64_t full = (seg_end - k0) / g.S;      // whole rounds inside this segment
+        if (full > 0 && sg.chunk_log2 == kBlocked) {
+            uint32_t *out = out_base + sg.out_off + (k0 - seg_start);
+            const uint32_t rounds = (uint32_t)min(full, (uint64_t)0x7FFFFFFFu);
+            if (sg.dtype == 0u)
+                run_fast<T, Q, 0>(g, buf, B, rel, prev, rounds, out);
+            else if (sg.dtype == 1u)
+                run_fast<T, Q, 1>(g, buf, B, rel, prev, rounds, out);
+            else
+                run_fast<T, Q, 2>(g, buf, B, rel, prev, rounds, out);
+            k0 += (uint64_t)rounds * g.S;
+        } else {
+            maybe_compact<T, Q>(g, buf, B, rel);
+            const uint32_t S_r = (uint32_t)min((uint64_t)g.S, w.total - k0);
+            round_general<T, Q>(g, buf + rel + tid, prev, S_r, k0, segs, si, seg_start, out_base);
+            round_sync<T>();
+            rel += S_r;
+            k0 += S_r;
+        }
+    }
+    for (uint32_t j = tid; j < g.N; j += T) st[j] = buf[rel + j];   // state write-back (Sec. 8)
+}
+
+// Runs the work item with the slot count Q = ceil(S / T) it needs, searching
+// the compiled counts QMAX, QMAX-1, ..., 1.  Returns false if none matches.
+template <int T, int QMAX>
+__device__ __forceinline__ bool dispatch_slots(uint32_t nq, const GenCtx &g, uint32_t *buf, uint32_t B,
+                                               const DevWork &w, const DevSeg *segs, uint32_t *out,
+                                               uint32_t *st)
+{
+    if (nq == (uint32_t)QMAX) {
+        run_item<T, QMAX>(g, buf, B, w, segs, out, st);
+        return true;
+    }
+    if constexpr (QMAX > 1)
+        return dispatch_slots<T, QMAX - 1>(nq, g, buf, B, w, segs, out, st);
+    else
+        return false;
+}
+
+template <int T, int QMAX>
+__global__ void __launch_bounds__(T, QMAX <= 6 ? 512 / T : (T >= 256 ? 1 : 256 / T)) k_generate(const LaunchArgs a)
+{
+    extern __shared__ __align__(16) uint32_t buf[];
+    __shared__ uint32_t s_item;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
+    const uint32_t B = a.buf_words;
+    uint32_t item = blockIdx.x;
+    for (;;) {
+        if (a.persistent) {
+            if (tid == 0) s_item = atomicAdd(a.counter, 1u);
+            __syncthreads();
+            item = s_item;
+        }
+        if (item >= a.nwork) break;
+        const DevWork w = a.work[item];
+        DevGen &gd = a.gens[w.gen];
+        GenCtx g;
+        g.N = gd.N;
+        g.M = gd.M;
+        g.mask = gd.mask;
+        g.sh1 = gd.sh1;
+        g.sh2 = gd.sh2;
+        g.S = g.N - g.M;
+        g.rec_r = gd.rec[lane & 15u];
+        g.tmp_r = gd.tmp[lane & 15u];
+        const uint32_t nq = (g.S + T - 1u) / T;
+        bool ok = nq <= (uint32_t)QMAX && 2u * g.N + nq * T + 32u <= B;
+        if (ok) {
+            uint32_t *st = a.state + gd.state_off;
+            for (uint32_t j = tid; j < g.N; j += T) buf[j] = st[j];
+            __syncthreads();
+            ok = dispatch_slots<T, QMAX>(nq, g, buf, B, w, a.segs + w.seg_begin, a.out, st);
+            if (ok && tid == 0) gd.count += w.total;
+        }
+        if (!ok && tid == 0) atomicOr(a.err, kErrBuffer);
+        __syncthreads();                                     // buffer and s_item reuse
+        if (!a.persistent) break;
+    }
+}
+
+}  // namespace dev
+}  // namespace mtgp

@@ -165,16 +165,17 @@ struct mtgp_state {
 
 namespace {
 
-const mtgp_config kDefaultConfig = {256u, 0u, 0u, 0u, 256u};
+const mtgp_config kDefaultConfig = {128u, 0u, 0u, 256u, 0u};
 
 mtgp_status check_config(const mtgp_config &c)
 {
-    if (c.threads < 32u || c.threads > 1024u || c.threads % 32u)
-        return fail(MTGP_EINVAL, "threads must be a multiple of 32 in [32, 1024], got %u", c.threads);
+    if (!threads_supported(c.threads))
+        return fail(MTGP_EINVAL, "threads must be 32, 64, 128, 256 or 512, got %u", c.threads);
     if (c.persistent > 1u) return fail(MTGP_EINVAL, "persistent must be 0 or 1");
     if (c.blocks_per_sm > 32u) return fail(MTGP_EINVAL, "blocks_per_sm must be <= 32");
     if (c.chunk < 32u || (c.chunk & (c.chunk - 1u)))
         return fail(MTGP_EINVAL, "chunk must be a power of two >= 32, got %u", c.chunk);
+    if (c.buffer_words > 57344u) return fail(MTGP_EINVAL, "buffer_words must be <= 57344 (224 KiB)");
     return MTGP_OK;
 }
 
@@ -297,20 +298,38 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
 {
     if (plan.work.empty()) return MTGP_OK;
     const mtgp_config &c = p->cfg;
-    // round size and ring
-    uint32_t wmax = 0, need = 0;
+    uint32_t nmax = 0, smax = 0;
     for (const DevWork &w : plan.work) {
         const DevGen &g = p->host_gens[w.gen];
-        const uint32_t wg = round_words(g.N, g.M, c.words_per_round, c.threads, kMaxQ);
-        wmax = std::max(wmax, wg);
+        nmax = std::max(nmax, g.N);
+        smax = std::max(smax, g.N - g.M);
     }
-    uint32_t qmax = 1;
-    while (qmax * c.threads < wmax && qmax < kMaxQ && c.threads <= max_threads_for_q(qmax * 2u)) qmax <<= 1;
+    const uint32_t qmax = kernel_slots(c.threads, (smax + c.threads - 1u) / c.threads);
+    if (!qmax)
+        return fail(MTGP_EINVAL, "rounds of %u words need more than %u threads x %u slots", smax, c.threads,
+                    max_slots(c.threads));
+    // shared buffer: at least 2N + T ceil(S/T) + 32 words (reads of the last
+    // column slot stay inside, compaction never overlaps); up to 32 rounds
+    // between compactions if the blocks wanted per SM fit
+    uint32_t need = 0;
     for (const DevWork &w : plan.work) {
         const DevGen &g = p->host_gens[w.gen];
-        need = std::max(need, g.N + round_words(g.N, g.M, c.words_per_round, c.threads, qmax));
+        const uint32_t S = g.N - g.M, span = (S + c.threads - 1u) / c.threads * c.threads;
+        need = std::max(need, 2u * g.N + span + 32u);
     }
-    const uint32_t ring = pow2_ceil(need);
+    uint32_t B = c.buffer_words;
+    if (!B) {
+        uint32_t per_sm = c.persistent ? (c.blocks_per_sm ? c.blocks_per_sm : 2u)
+                                       : (uint32_t)std::min<size_t>(8, (plan.work.size() + p->sm_count - 1) /
+                                                                           (size_t)p->sm_count);
+        per_sm = std::max(per_sm, 1u);
+        const uint32_t budget = std::min(57344u, (uint32_t)((227u * 1024u / per_sm - 1024u) / 4u));
+        B = std::min(2u * nmax + 32u * smax + 32u, budget);
+        B = std::max(B, std::min(need + smax, 57344u));
+        B = std::max(B, need);
+    }
+    if (B < need) return fail(MTGP_EINVAL, "buffer_words %u < 2N + T ceil(S/T) + 32 = %u", B, need);
+    if (B > 57344u) return fail(MTGP_EINVAL, "state too large for shared memory (%u words)", B);
     // upload
     const size_t wbytes = plan.work.size() * sizeof(DevWork);
     const size_t sbytes = plan.segs.size() * sizeof(DevSeg);
@@ -325,7 +344,7 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     if (c.persistent) {
         CU(cudaMemsetAsync(p->d_ctl, 0, sizeof(unsigned), s), "reset work counter");
         int occ = 0;
-        CU(generate_occupancy(c.threads, qmax, ring, &occ), "occupancy");
+        CU(generate_occupancy(c.threads, qmax, B, &occ), "occupancy");
         if (occ < 1) return fail(MTGP_EINVAL, "configuration does not fit on an SM");
         const int per_sm = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, occ) : occ;
         grid = std::min<uint32_t>(grid, (uint32_t)(per_sm * p->sm_count));
@@ -339,10 +358,9 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     a.counter = p->d_ctl;
     a.err = p->d_ctl + 1;
     a.nwork = (uint32_t)plan.work.size();
-    a.ring_words = ring;
-    a.wpr_cap = c.words_per_round;
+    a.buf_words = B;
     a.persistent = c.persistent;
-    CU(launch_generate(a, c.threads, grid, qmax, s), "generate kernel launch");
+    CU(launch_generate(a, c.threads, qmax, grid, s), "generate kernel launch");
     CU(cudaEventRecord(p->ev_done, s), "cudaEventRecord");
     p->last_stream = s;
     p->used = true;
@@ -788,14 +806,12 @@ mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
     if (st != MTGP_OK) return st;
     const mtgp_config orig = p->cfg;
     std::vector<mtgp_config> cands;
-    for (uint32_t threads : {128u, 256u, 512u, 1024u})
-        for (uint32_t wpr : {0u, 256u, 512u, 1024u})
-            for (uint32_t pers : {0u, 1u})
-                for (uint32_t bps : {0u, 1u, 2u, 3u}) {
-                    if (!pers && bps) continue;
-                    if (wpr && wpr < threads) continue;
-                    cands.push_back(mtgp_config{threads, wpr, pers, bps, orig.chunk});
-                }
+    for (uint32_t threads : {32u, 64u, 128u, 256u, 512u})
+        for (uint32_t pers : {0u, 1u})
+            for (uint32_t bps : {0u, 1u, 2u, 3u, 4u, 6u, 8u}) {
+                if (!pers && bps) continue;
+                cands.push_back(mtgp_config{threads, pers, bps, orig.chunk, 0u});
+            }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0), "cudaEventCreate");
     CU(cudaEventCreate(&e1), "cudaEventCreate");

@@ -39,7 +39,7 @@ struct alignas(16) DevWork {
 static_assert(sizeof(DevWork) == 32, "DevWork layout");
 
 // Error bits the kernels may set in LaunchArgs::err.
-constexpr unsigned kErrRing = 1u;    // a generator did not fit the launch's ring
+constexpr unsigned kErrBuffer = 1u;  // a generator did not fit the launch's shape or buffer
 
 struct LaunchArgs {
     DevGen *gens;
@@ -50,36 +50,37 @@ struct LaunchArgs {
     unsigned *counter;            // persistent work counter, zero at launch
     unsigned *err;
     uint32_t nwork;
-    uint32_t ring_words;          // power of two, >= N + round size of every item
-    uint32_t wpr_cap;             // cap on the round size
+    uint32_t buf_words;           // shared buffer, >= 2N + S + 32 words for every item
     uint32_t persistent;
 };
 
-constexpr uint32_t kMaxQ = 8;       // rounds may be up to kMaxQ x threads words
-
-// Largest block for a kernel instance that keeps up to q words per thread in
-// flight (keeps 4q live words per thread in registers without spilling).
-__host__ __device__ constexpr uint32_t max_threads_for_q(uint32_t q)
+// Generation kernels are compiled per block size T and per maximum slot
+// count QMAX: k_generate<T, QMAX> runs generators whose round size S = N - M
+// needs ceil(S / T) <= QMAX column slots per thread.  Slot counts compiled:
+#define MTGP_QMAX_LIST 2, 3, 4, 6, 8, 11, 12
+//   T = 32: 4, 11    T = 64: 3, 6, 12    T = 128: 3, 6, 11    T = 256: 2, 3, 6
+//   T = 512: 2, 4, 8
+__host__ __device__ constexpr uint32_t max_slots(uint32_t threads)
 {
-    return q <= 2u ? 1024u : 512u;
+    return threads == 32u ? 11u : threads == 64u ? 12u : threads == 128u ? 11u : threads == 256u ? 6u
+         : threads == 512u ? 8u : 0u;
 }
 
-// Round size of a generator: min(cap, N - M) (Sec. 3.2), rounded down to a
-// whole number of warps when at least one warp, and at most qmax x threads.
-__host__ __device__ inline uint32_t round_words(uint32_t N, uint32_t M, uint32_t cap, uint32_t threads, uint32_t qmax)
-{
-    uint32_t w = N - M;
-    if (cap && cap < w) w = cap;
-    if (w >= 32u) w &= ~31u;
-    if (w > qmax * threads) w = qmax * threads;
-    return w;
-}
+typedef void (*GenKernel)(const LaunchArgs);
+GenKernel gen_kernel_t32(uint32_t qmax);
+GenKernel gen_kernel_t64(uint32_t qmax);
+GenKernel gen_kernel_t128(uint32_t qmax);
+GenKernel gen_kernel_t256(uint32_t qmax);
+GenKernel gen_kernel_t512(uint32_t qmax);
 
+bool threads_supported(uint32_t threads);
+// Smallest compiled QMAX >= nq for this block size, 0 if none.
+uint32_t kernel_slots(uint32_t threads, uint32_t nq);
 cudaError_t launch_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
                         const uint64_t *seeds, uint32_t first, uint32_t count, cudaStream_t s);
-cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t grid, uint32_t qmax,
+cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t qmax, uint32_t grid,
                             cudaStream_t s);
-cudaError_t generate_occupancy(uint32_t threads, uint32_t qmax, uint32_t ring_words, int *blocks_per_sm);
+cudaError_t generate_occupancy(uint32_t threads, uint32_t qmax, uint32_t buf_words, int *blocks_per_sm);
 cudaError_t launch_fill(uint32_t *buf, uint64_t words, uint32_t pattern, cudaStream_t s);
 
 }  // namespace mtgp

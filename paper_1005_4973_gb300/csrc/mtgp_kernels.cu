@@ -1,21 +1,6 @@
-// MTGP generation kernels for sm_103a.
-//
-// One thread block owns one generator at a time (Sec. 3.2).  Its state lives
-// in a shared-memory ring X[0 .. L) holding x_k at X[k mod L] (the array of
-// Knuth's Algorithm A, Sec. 3.1), with L a power of two >= N + W so that one
-// round -- W <= N - M consecutive words x_{N+i}, all independent (Sec. 3.2) --
-// never overwrites a word the same round still reads.  A round needs one
-// block barrier.  Each output is tempered with x_{M-1+i} (Sec. 3.7) and, for
-// float outputs, filled into a float's mantissa (Sec. 6), then streamed to HBM.
-//
-// GB300 choices (not in the paper, whose GPUs had 16 banks and a texture
-// cache): the 16-entry tables are held one entry per lane and read with a
-// width-16 warp shuffle, which masks the index to its four LSBs in hardware
-// and never conflicts; a round issues all of its shared-memory loads before
-// any arithmetic so their latencies overlap; the round size is a whole number
-// of warps, and warps with no word in a round skip it; work items (a
-// generator's consecutive requests) can be pulled from a device counter by a
-// persistent grid, longest first.
+// MTGP kernels for sm_103a other than the generation kernel (which lives in
+// mtgp_device.cuh and the per-block-size units mtgp_gen_t*.cu): state seeding,
+// the write-only bandwidth probe, and the launchers.
 #include "mtgp_internal.h"
 
 namespace mtgp {
@@ -56,116 +41,6 @@ __global__ void k_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
     }
 }
 
-// Output of Sec. 3.7 / Sec. 6 from the new word xn and the looked-up table
-// entry v (tmptbl for integers, the single-precision table for floats).
-template <int DT>
-__device__ __forceinline__ uint32_t finish(uint32_t xn, uint32_t v)
-{
-    if (DT == 0) return xn ^ v;
-    const uint32_t bits = (xn >> 9) ^ v;                     // float in [1, 2)
-    if (DT == 1) return bits;
-    return __float_as_uint(__fsub_rn(__uint_as_float(bits), 1.0f));   // exact
-}
-
-// Runs one segment (n numbers of one dtype) of the current work item.
-// `base` is the ring index of x_k, the oldest live state word.
-template <int QMAX, int DT>
-__device__ __forceinline__ void run_segment(uint32_t *ring, uint32_t Lm, uint32_t &base,
-                                            uint32_t N, uint32_t M, uint32_t mask,
-                                            uint32_t sh1, uint32_t sh2, uint32_t W,
-                                            uint32_t rec_r, uint32_t tbl_r, const DevSeg &seg,
-                                            uint32_t *out)
-{
-    const uint32_t T = blockDim.x, tid = threadIdx.x, wbase = tid & ~31u;
-    uint32_t *o = out + seg.out_off;
-    const bool blocked = seg.chunk_log2 == kBlocked;
-    const uint64_t cmask = blocked ? 0ull : ((1ull << seg.chunk_log2) - 1ull);
-    for (uint64_t done = 0; done < seg.n; done += W) {
-        const uint32_t cnt = (uint32_t)min((uint64_t)W, seg.n - done);
-        uint32_t x0[QMAX], x1[QMAX], xm[QMAX], xt[QMAX];
-#pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
-            if (q * T + wbase < cnt) {                       // warp-uniform
-                const uint32_t i = base + q * T + tid;
-                x0[q] = ring[i & Lm];
-                x1[q] = ring[(i + 1u) & Lm];
-                xm[q] = ring[(i + M) & Lm];
-                xt[q] = ring[(i + M - 1u) & Lm];
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
-            if (q * T + wbase < cnt) {
-                const uint32_t j = q * T + tid;
-                // recursion g (Sec. 3.6)
-                uint32_t t = x1[q] ^ (x0[q] & mask);
-                t ^= t << sh1;
-                const uint32_t u = t ^ (xm[q] >> sh2);
-                const uint32_t xn = u ^ __shfl_sync(0xffffffffu, rec_r, (int)u, 16);
-                // tempering h (Sec. 3.7) with x_{M-1+i}
-                uint32_t s = xt[q] ^ (xt[q] >> 16);
-                s ^= s >> 8;
-                const uint32_t v = __shfl_sync(0xffffffffu, tbl_r, (int)s, 16);
-                const uint32_t r = finish<DT>(xn, v);
-                if (j < cnt) {
-                    ring[(base + j + N) & Lm] = xn;
-                    const uint64_t k = done + j;
-                    const uint64_t idx = blocked ? k : ((k >> seg.chunk_log2) * seg.stride + (k & cmask));
-                    __stcs(o + idx, r);
-                }
-            }
-        }
-        base += cnt;
-        __syncthreads();
-    }
-}
-
-template <int QMAX>
-__global__ void __launch_bounds__(max_threads_for_q(QMAX)) k_generate(const LaunchArgs a)
-{
-    extern __shared__ __align__(16) uint32_t ring[];
-    __shared__ uint32_t s_item;
-    const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31u;
-    const uint32_t Lm = a.ring_words - 1u;
-    uint32_t item = blockIdx.x;
-    for (;;) {
-        if (a.persistent) {
-            if (tid == 0) s_item = atomicAdd(a.counter, 1u);
-            __syncthreads();
-            item = s_item;
-        }
-        if (item >= a.nwork) break;
-        const DevWork w = a.work[item];
-        DevGen &g = a.gens[w.gen];
-        const uint32_t N = g.N, M = g.M, mask = g.mask, sh1 = g.sh1, sh2 = g.sh2;
-        const uint32_t W = round_words(N, M, a.wpr_cap, T, QMAX);
-        if (N + W <= a.ring_words && W > 0u) {
-            const uint32_t rec_r = g.rec[lane & 15u];
-            const uint32_t tmp_r = g.tmp[lane & 15u];
-            const uint32_t flt_r = 0x3F800000u | (tmp_r >> 9);  // single-precision table (Sec. 6)
-            uint32_t *st = a.state + g.state_off;
-            for (uint32_t j = tid; j < N; j += T) ring[j] = st[j];
-            __syncthreads();
-            uint32_t base = 0;
-            for (uint32_t s = 0; s < w.seg_count; ++s) {
-                const DevSeg seg = a.segs[w.seg_begin + s];
-                if (seg.dtype == 0u)
-                    run_segment<QMAX, 0>(ring, Lm, base, N, M, mask, sh1, sh2, W, rec_r, tmp_r, seg, a.out);
-                else if (seg.dtype == 1u)
-                    run_segment<QMAX, 1>(ring, Lm, base, N, M, mask, sh1, sh2, W, rec_r, flt_r, seg, a.out);
-                else
-                    run_segment<QMAX, 2>(ring, Lm, base, N, M, mask, sh1, sh2, W, rec_r, flt_r, seg, a.out);
-            }
-            for (uint32_t j = tid; j < N; j += T) st[j] = ring[(base + j) & Lm];
-            if (tid == 0) g.count += w.total;
-        } else if (tid == 0) {
-            atomicOr(a.err, kErrRing);
-        }
-        __syncthreads();                                     // ring and s_item reuse
-        if (!a.persistent) break;
-    }
-}
-
 // Write-only bandwidth probe: 16-byte streaming stores over a grid-stride loop.
 __global__ void k_fill(uint4 *buf, uint64_t n16, uint32_t pattern)
 {
@@ -176,15 +51,29 @@ __global__ void k_fill(uint4 *buf, uint64_t n16, uint32_t pattern)
     }
 }
 
-template <int Q>
-cudaError_t launch_q(const LaunchArgs &a, uint32_t threads, uint32_t grid, cudaStream_t s)
+GenKernel pick(uint32_t threads, uint32_t qmax)
 {
-    const size_t smem = (size_t)a.ring_words * sizeof(uint32_t);
-    k_generate<Q><<<grid, threads, smem, s>>>(a);
-    return cudaGetLastError();
+    switch (threads) {
+    case 32: return gen_kernel_t32(qmax);
+    case 64: return gen_kernel_t64(qmax);
+    case 128: return gen_kernel_t128(qmax);
+    case 256: return gen_kernel_t256(qmax);
+    case 512: return gen_kernel_t512(qmax);
+    default: return nullptr;
+    }
 }
 
 }  // namespace
+
+bool threads_supported(uint32_t threads) { return max_slots(threads) != 0u; }
+
+uint32_t kernel_slots(uint32_t threads, uint32_t nq)
+{
+    static const uint32_t compiled[] = {MTGP_QMAX_LIST};
+    for (uint32_t q : compiled)
+        if (q >= nq && pick(threads, q)) return q;
+    return 0;
+}
 
 cudaError_t launch_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
                         const uint64_t *seeds, uint32_t first, uint32_t count, cudaStream_t s)
@@ -194,28 +83,30 @@ cudaError_t launch_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
     return cudaGetLastError();
 }
 
-cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t grid, uint32_t qmax,
+cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t qmax, uint32_t grid,
                             cudaStream_t s)
 {
-    switch (qmax) {
-    case 1: return launch_q<1>(a, threads, grid, s);
-    case 2: return launch_q<2>(a, threads, grid, s);
-    case 4: return launch_q<4>(a, threads, grid, s);
-    case 8: return launch_q<8>(a, threads, grid, s);
-    default: return cudaErrorInvalidValue;
+    GenKernel k = pick(threads, qmax);
+    if (!k) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)a.buf_words * sizeof(uint32_t);
+    if (smem > 48u * 1024u) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
     }
+    k<<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
-cudaError_t generate_occupancy(uint32_t threads, uint32_t qmax, uint32_t ring_words, int *blocks_per_sm)
+cudaError_t generate_occupancy(uint32_t threads, uint32_t qmax, uint32_t buf_words, int *blocks_per_sm)
 {
-    const size_t smem = (size_t)ring_words * sizeof(uint32_t);
-    switch (qmax) {
-    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_generate<1>, threads, smem);
-    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_generate<2>, threads, smem);
-    case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_generate<4>, threads, smem);
-    case 8: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_generate<8>, threads, smem);
-    default: return cudaErrorInvalidValue;
+    GenKernel k = pick(threads, qmax);
+    if (!k) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)buf_words * sizeof(uint32_t);
+    if (smem > 48u * 1024u) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
     }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
 }
 
 cudaError_t launch_fill(uint32_t *buf, uint64_t words, uint32_t pattern, cudaStream_t s)

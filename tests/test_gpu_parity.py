@@ -81,26 +81,81 @@ MIXED = [WL.GenSpec(11213, 1, 0, 0), WL.GenSpec(23209, 2, 1, 1), WL.GenSpec(4449
 RAGGED = [1, 31, 33, 255, 257, 1000, 4097, 12345]
 
 
-@pytest.mark.parametrize("threads", [32, 64, 96, 128, 256, 512, 1024])
+def _round_size(spec):
+    p = oracle_params(spec)
+    return p.N - p.pos
+
+
+@pytest.mark.parametrize("threads", [32, 64, 128, 256, 512])
 @pytest.mark.parametrize("persistent", [0, 1])
 def test_launch_shapes(threads, persistent):
+    from paper_1005_4973_gb300._lib import MAX_SLOTS
+    gens = [g for g in MIXED if _round_size(g) <= threads * MAX_SLOTS[threads]]
     reqs, off = [], 0
-    for g in range(len(MIXED)):
+    for g in range(len(gens)):
         for k, n in enumerate(RAGGED[g % 3::3] + [RAGGED[(g + 1) % len(RAGGED)]]):
             reqs.append((g, (g + k) % 3, n, off))
             off += n
-    pool, out = _run(MIXED, reqs, config=dict(threads=threads, persistent=persistent))
-    _check_blocked(MIXED, reqs, out, pool)
+    pool, out = _run(gens, reqs, config=dict(threads=threads, persistent=persistent))
+    _check_blocked(gens, reqs, out, pool)
 
 
-@pytest.mark.parametrize("wpr", [1, 7, 32, 33, 64, 100, 256, 300, 1000])
-def test_round_size_caps(wpr):
-    reqs, off = [], 0
-    for g in range(len(MIXED)):
-        reqs.append((g, WL.U32, 5003, off))
-        off += 5003
-    pool, out = _run(MIXED, reqs, config=dict(threads=128, words_per_round=wpr))
-    _check_blocked(MIXED, reqs, out, pool)
+@pytest.mark.parametrize("threads", [32, 64, 128, 256, 512])
+def test_every_slot_count(threads):
+    """Generators whose round size S = N - M needs each slot count 1 .. max:
+    reduced-exponent and synthetic sets with M chosen to hit S = T q and
+    S = T q - 31 (fullest and emptiest last slot)."""
+    import paper_1005_4973_gb300 as M
+    from paper_1005_4973_gb300._lib import MAX_SLOTS
+    ps, ops, n = [], [], 3001
+    for q in range(1, MAX_SLOTS[threads] + 1):
+        for S in {threads * q, max(1, threads * q - 31)}:
+            # smallest exponent whose N leaves room for M >= 2 with N - M = S
+            N = S + 2 + (q % 5)
+            mexp = 32 * N - 17
+            if N > 4096:
+                continue
+            lp = M.mtgp_params_draw(mexp, q, q)
+            o = O.params_draw(mexp, q, q)
+            Mpos = N - S
+            lp.pos = Mpos
+            ops.append(O.params_from_fields(mexp, Mpos, o.sh1, o.sh2, q, list(o.R), list(o.T)))
+            ps.append(lp)
+    pool = M.Pool(ps, list(range(len(ps))), [11] * len(ps))
+    pool.set_config(threads=threads)
+    out = torch.zeros(n * len(ps), dtype=torch.int32, device="cuda")
+    pool.generate([(i, i % 3, n, i * n) for i in range(len(ps))], out)
+    o = as_u32(out)
+    for i, op in enumerate(ops):
+        st = O.seed_state(op, i, 11)
+        assert np.array_equal(o[i * n:(i + 1) * n], O.generate(op, st, n, i % 3)), (op.N, op.pos)
+        assert np.array_equal(pool.read_state(i), st)
+
+
+@pytest.mark.parametrize("extra", [0, 1, 7, 300, 2000])
+def test_small_buffers_force_compaction(extra):
+    # buffer_words = 2N + T ceil(S/T) + 32 + extra: compaction every round or two
+    gens = MIXED[:3]
+    ps = [oracle_params(g) for g in gens]
+    need = max(2 * p.N + -(-(p.N - p.pos) // 128) * 128 + 32 for p in ps)
+    reqs = [(g, g % 3, 20011, 20011 * g) for g in range(3)]
+    pool, out = _run(gens, reqs, config=dict(threads=128, buffer_words=need + extra))
+    _check_blocked(gens, reqs, out, pool)
+
+
+def test_too_small_buffer_rejected():
+    import paper_1005_4973_gb300 as M
+    pool = lib_pool(MIXED[:1])
+    p = oracle_params(MIXED[0])
+    pool.set_config(buffer_words=2 * p.N + -(-(p.N - p.pos) // 128) * 128 + 31)
+    out = torch.zeros(16, dtype=torch.int32, device="cuda")
+    with pytest.raises(M.MTGPError):
+        pool.generate([(0, 0, 16, 0)], out)
+    pool.set_config(buffer_words=0, threads=32)
+    big = lib_pool([MIXED[2]])                      # S > 32 x 11: no 32-thread shape
+    big.set_config(threads=32)
+    with pytest.raises(M.MTGPError):
+        big.generate([(0, 0, 16, 0)], out)
 
 
 def test_random_shift_sets():
@@ -191,6 +246,8 @@ def test_bad_requests_rejected():
             pool.generate(reqs, out, layout=layout)
     with pytest.raises(M.MTGPError):
         pool.set_config(threads=48)
+    with pytest.raises(M.MTGPError):
+        pool.set_config(threads=1024)
     with pytest.raises(M.MTGPError):
         pool.set_config(chunk=100)
 

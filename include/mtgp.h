@@ -90,19 +90,24 @@ typedef struct mtgp_request {
 } mtgp_request;
 
 /* Launch configuration of a pool (chosen by mtgp_autotune or set by hand).
- * A generator runs in rounds of S = N - M words (Sec. 3.2); each thread of a
- * block owns ceil(S / threads) of the S columns, at most 11 (32 threads),
- * 12 (64), 11 (128), 6 (256) or 8 (512). */
+ * A generator runs in rounds of S = N - M words (Sec. 3.2).  Plain form: each
+ * of the `threads` threads owns ceil(S / threads) of the S columns and also
+ * tempers and stores them.  Split form: the first half of the block runs the
+ * recursion (owning ceil(S / (threads / 2)) columns each) and the second half
+ * tempers, converts and stores finished rounds. */
 typedef struct mtgp_config {
-    uint32_t threads;          /* threads per block: 32, 64, 128, 256 or 512          */
+    uint32_t threads;          /* threads per block: plain 32, 64, 128, 256, 512
+                                  (at most 11, 12, 11, 6, 8 columns per thread);
+                                  split 128, 256, 512, 1024 (at most 12, 11, 6, 3) */
     uint32_t persistent;       /* 1: grid of SMs x blocks_per_sm blocks taking work
                                   items longest first from a device counter;
                                   0: one block per work item                         */
     uint32_t blocks_per_sm;    /* persistent grid occupancy, 0 = what fits            */
     uint32_t chunk;            /* interleaved layout chunk, power of two >= 32       */
     uint32_t buffer_words;     /* shared-memory words per block, 0 = sized from the
-                                  launch (>= 2N + threads ceil(S / threads) + 32
-                                  is required)                                        */
+                                  launch (>= 2N + owners ceil(S / owners) + 32 is
+                                  required, owners = threads or threads / 2)         */
+    uint32_t split;            /* 0 plain form, 1 split (warp-specialised) form      */
 } mtgp_config;
 
 /* ---- library ------------------------------------------------------------ */
@@ -239,7 +244,7 @@ mtgp_status mtgp_pool_load(mtgp_pool *p, const void *host_buf, size_t bytes);
 void mtgp_pool_destroy(mtgp_pool *p);
 
 /*
- * Picks threads, persistent mode and occupancy
+ * Picks the form (plain or split), threads, persistent mode and occupancy
  * for this pool by timing candidate configurations on `stream` with the given
  * requests written to dev_scratch (caller-owned, large enough for them).  The
  * generators' states are saved before and restored after, so tuning does not

@@ -21,6 +21,8 @@ MTGP_MAX_N = 4096
 # block sizes compiled into the library and the column slots per thread each
 # supports (mirrors max_slots in the CUDA sources)
 MAX_SLOTS = {32: 11, 64: 12, 128: 11, 256: 6, 512: 8}
+# split form: block size -> columns per recursion thread (threads / 2 own columns)
+MAX_SLOTS_SPLIT = {128: 12, 256: 11, 512: 6, 1024: 3}
 STATUS_NAMES = {0: "MTGP_OK", 1: "MTGP_EINVAL", 2: "MTGP_ENOMEM", 3: "MTGP_ECUDA",
                 4: "MTGP_ETIMEOUT", 5: "MTGP_EBUSY"}
 
@@ -43,7 +45,7 @@ class mtgp_request(ctypes.Structure):
 
 class mtgp_config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
-                ("threads", "persistent", "blocks_per_sm", "chunk", "buffer_words")]
+                ("threads", "persistent", "blocks_per_sm", "chunk", "buffer_words", "split")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -256,6 +256,303 @@ __device__ __forceinline__ bool dispatch_slots(uint32_t nq, const GenCtx &g, uin
         return false;
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised form.  A block of 2 RT threads runs one generator with two
+// groups: the first RT threads (recursion group) compute the rounds of the
+// recursion (Sec. 3.6) into the shared buffer; the other RT threads (output
+// group) temper (Sec. 3.7), convert (Sec. 6) and store the words of rounds
+// the recursion group has finished.  The recursion group's critical path per
+// round is then two shared loads, four integer operations, one table
+// shuffle, one shared store and a barrier among its own warps; the output
+// group's work has no dependence between words or rounds.
+//
+// Hand-off, with named barriers (ids: 1 recursion-group barrier; 2 .. 2+K-1
+// FULL; 2+K .. 2+2K-1 EMPTY; K = kRing):
+//   recursion, round r: if the buffer must be compacted, sync EMPTY of every
+//     round not yet drained, then compact; otherwise, if r - K >= drained,
+//     sync EMPTY[(r-K) % K]; compute round r; sync the recursion barrier;
+//     arrive FULL[r % K].  After the last round, sync EMPTY of every round not
+//     yet drained.
+//   output, round r: sync FULL[r % K]; temper, convert, store; arrive
+//     EMPTY[r % K].
+// Every arrival is matched by exactly one sync of the other group, no group
+// arrives twice at a barrier before it completes, and the recursion group
+// overwrites buffer words (compaction) only after the output group consumed
+// every earlier round (checked by the CPU model in tests).
+constexpr uint32_t kRing = 4;
+constexpr uint32_t kBarRec = 1;
+
+// Named-barrier operations are warp-aligned: the warp is reconverged first.
+__device__ __forceinline__ void nb_sync(uint32_t id, uint32_t n)
+{
+    __syncwarp();
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void nb_arrive(uint32_t id, uint32_t n)
+{
+    __syncwarp();
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ uint32_t bar_full(uint32_t r) { return 2u + r % kRing; }
+__device__ __forceinline__ uint32_t bar_empty(uint32_t r) { return 2u + kRing + r % kRing; }
+
+// Recursion group: all rounds of one work item.  rt = thread index in the group.
+template <int RT, int Q>
+__device__ __forceinline__ void split_recursion(const GenCtx &g, uint32_t *buf, uint32_t B, uint64_t total,
+                                                uint32_t rt, uint32_t *st)
+{
+    constexpr int F = Q - 1;
+    constexpr uint32_t ALL = 2u * RT;
+    const bool tail_warp = (uint32_t)F * RT + (rt & ~31u) < g.S;
+    uint32_t prev[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)                              // x_{c+M}, c = column
+        prev[q] = (q * RT + rt < g.S) ? buf[q * RT + rt + g.M] : 0u;
+    const uint32_t rounds = (uint32_t)((total + g.S - 1u) / g.S);
+    uint32_t rel = 0, drained = 0;
+    uint64_t k0 = 0;
+    for (uint32_t r = 0; r < rounds; ++r) {
+        const uint32_t S_r = (uint32_t)min((uint64_t)g.S, total - k0);
+        if (rel + g.N + (uint32_t)(Q * RT) + 32u > B) {      // compaction
+            for (uint32_t j = (r > drained + kRing ? r - kRing : drained); j < r; ++j)
+                nb_sync(bar_empty(j), ALL);
+            drained = r;
+            for (uint32_t j = rt; j < g.N; j += RT) buf[j] = buf[rel + j];
+            nb_sync(kBarRec, RT);
+            rel = 0;
+        } else if (r >= drained + kRing) {
+            nb_sync(bar_empty(r - kRing), ALL);
+        }
+        const uint32_t *x = buf + rel + rt;
+        uint32_t *xn_p = buf + rel + rt + g.N;
+        uint32_t a[Q], b[Q];
+#pragma unroll
+        for (int q = 0; q < F; ++q) {
+            a[q] = x[q * RT];
+            b[q] = x[q * RT + 1];
+        }
+#pragma unroll
+        for (int q = 0; q < F; ++q) {
+            const uint32_t t = b[q] ^ (a[q] & g.mask);
+            a[q] = t ^ (t << g.sh1) ^ (prev[q] >> g.sh2);
+        }
+#pragma unroll
+        for (int q = 0; q < F; ++q) {
+            const uint32_t xn = a[q] ^ __shfl_sync(0xffffffffu, g.rec_r, (int)a[q], 16);
+            if (q * RT + rt < S_r) xn_p[q * RT] = xn;
+            prev[q] = xn;
+        }
+        if (tail_warp) {
+            const uint32_t a0 = x[F * RT], b0 = x[F * RT + 1];
+            const uint32_t t = b0 ^ (a0 & g.mask);
+            const uint32_t u = t ^ (t << g.sh1) ^ (prev[F] >> g.sh2);
+            const uint32_t xn = u ^ __shfl_sync(0xffffffffu, g.rec_r, (int)u, 16);
+            if (F * RT + rt < S_r) {
+                xn_p[F * RT] = xn;
+                prev[F] = xn;
+            }
+        }
+        nb_sync(kBarRec, RT);
+        __threadfence_block();
+        nb_arrive(bar_full(r), ALL);
+        rel += S_r;
+        k0 += S_r;
+    }
+    for (uint32_t j = (rounds > drained + kRing ? rounds - kRing : drained); j < rounds; ++j)
+        nb_sync(bar_empty(j), ALL);
+    for (uint32_t j = rt; j < g.N; j += RT) st[j] = buf[rel + j];   // state write-back (Sec. 8)
+}
+
+// Output group: one round's Q slots inside one blocked segment of dtype DT.
+template <int RT, int Q, int DT>
+__device__ __forceinline__ void split_out_fast(const GenCtx &g, const uint32_t *x, uint32_t *__restrict__ out,
+                                               bool tail_warp, bool tail_lane)
+{
+    constexpr int F = Q - 1;
+    const uint32_t *xt_p = x + (g.M - 1u);
+    const uint32_t *xn_p = x + g.N;
+    uint32_t a[Q], c[Q];
+#pragma unroll
+    for (int q = 0; q < F; ++q) {
+        a[q] = xn_p[q * RT];
+        c[q] = xt_p[q * RT];
+    }
+#pragma unroll
+    for (int q = 0; q < F; ++q) {
+        uint32_t s = c[q] ^ (c[q] >> 16);
+        s ^= s >> 8;
+        c[q] = s;
+    }
+#pragma unroll
+    for (int q = 0; q < F; ++q)
+        __stcs(out + q * RT, finish(DT, a[q] ^ __shfl_sync(0xffffffffu, g.tmp_r, (int)c[q], 16)));
+    if (tail_warp) {
+        const uint32_t xn = xn_p[F * RT], xt = xt_p[F * RT];
+        uint32_t s = xt ^ (xt >> 16);
+        s ^= s >> 8;
+        const uint32_t v = __shfl_sync(0xffffffffu, g.tmp_r, (int)s, 16);
+        if (tail_lane) __stcs(out + F * RT, finish(DT, xn ^ v));
+    }
+}
+
+// Output group: full rounds inside one blocked segment of dtype DT.  Only the
+// shared reads of a round must be finished before EMPTY is signalled, and
+// they are (the stores consume their values), so no fence is needed here.
+template <int RT, int Q, int DT>
+__device__ __forceinline__ void split_out_run(const GenCtx &g, const uint32_t *buf, uint32_t B, uint32_t &rel,
+                                              uint32_t &r, uint32_t rounds, uint32_t *out, uint32_t rt)
+{
+    constexpr int F = Q - 1;
+    constexpr uint32_t ALL = 2u * RT;
+    const bool tail_warp = (uint32_t)F * RT + (rt & ~31u) < g.S;
+    const bool tail_lane = (uint32_t)F * RT + rt < g.S;
+    out += rt;
+    for (uint32_t i = 0; i < rounds; ++i, ++r) {
+        if (rel + g.N + (uint32_t)(Q * RT) + 32u > B) rel = 0;   // same rule as the recursion group
+        nb_sync(bar_full(r), ALL);
+        split_out_fast<RT, Q, DT>(g, buf + rel + rt, out, tail_warp, tail_lane);
+        nb_arrive(bar_empty(r), ALL);
+        rel += g.S;
+        out += g.S;
+    }
+}
+
+// Output group: all rounds of one work item.
+template <int RT, int Q>
+__device__ __forceinline__ void split_output(const GenCtx &g, uint32_t *buf, uint32_t B, const DevWork &w,
+                                             const DevSeg *segs, uint32_t *out_base, uint32_t rt)
+{
+    constexpr uint32_t ALL = 2u * RT;
+    uint32_t rel = 0, si = 0, r = 0;
+    uint64_t k0 = 0, seg_start = 0, seg_end = segs[0].n;
+    while (k0 < w.total) {
+        while (k0 >= seg_end) {                              // skip finished segments
+            ++si;
+            seg_start = seg_end;
+            seg_end += segs[si].n;
+        }
+        const DevSeg sg = segs[si];
+        const uint64_t full = (seg_end - k0) / g.S;          // whole rounds inside this segment
+        if (full > 0 && sg.chunk_log2 == kBlocked) {
+            uint32_t *out = out_base + sg.out_off + (k0 - seg_start);
+            const uint32_t rounds = (uint32_t)min(full, (uint64_t)0x7FFFFFFFu);
+            if (sg.dtype == 0u)
+                split_out_run<RT, Q, 0>(g, buf, B, rel, r, rounds, out, rt);
+            else if (sg.dtype == 1u)
+                split_out_run<RT, Q, 1>(g, buf, B, rel, r, rounds, out, rt);
+            else
+                split_out_run<RT, Q, 2>(g, buf, B, rel, r, rounds, out, rt);
+            k0 += (uint64_t)rounds * g.S;
+            continue;
+        }
+        // a round that is partial or spans segments (any layout): per-word routing
+        const uint32_t S_r = (uint32_t)min((uint64_t)g.S, w.total - k0);
+        if (rel + g.N + (uint32_t)(Q * RT) + 32u > B) rel = 0;
+        nb_sync(bar_full(r), ALL);
+        const uint32_t *x = buf + rel + rt;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if (q * RT + (rt & ~31u) < S_r) {
+                const uint32_t xn = x[g.N + q * RT], xt = x[g.M - 1u + q * RT];
+                uint32_t s = xt ^ (xt >> 16);
+                s ^= s >> 8;
+                const uint32_t o = xn ^ __shfl_sync(0xffffffffu, g.tmp_r, (int)s, 16);
+                if (q * RT + rt < S_r) {
+                    const uint64_t k = k0 + q * RT + rt;
+                    uint32_t s2 = si;
+                    uint64_t start = seg_start, end = seg_end;
+                    while (k >= end) {
+                        ++s2;
+                        start = end;
+                        end += segs[s2].n;
+                    }
+                    const DevSeg sg2 = segs[s2];
+                    const uint64_t kk = k - start;
+                    const uint64_t idx = sg2.chunk_log2 == kBlocked
+                                             ? kk
+                                             : (kk >> sg2.chunk_log2) * sg2.stride +
+                                                   (kk & ((1ull << sg2.chunk_log2) - 1ull));
+                    __stcs(out_base + sg2.out_off + idx, finish(sg2.dtype, o));
+                }
+            }
+        }
+        nb_arrive(bar_empty(r), ALL);
+        ++r;
+        rel += S_r;
+        k0 += S_r;
+    }
+}
+
+template <int RT, int Q>
+__device__ __forceinline__ void run_item_split(const GenCtx &g, uint32_t *buf, uint32_t B, const DevWork &w,
+                                               const DevSeg *segs, uint32_t *out, uint32_t *st)
+{
+    const uint32_t tid = threadIdx.x;
+    if (tid < (uint32_t)RT)
+        split_recursion<RT, Q>(g, buf, B, w.total, tid, st);
+    else
+        split_output<RT, Q>(g, buf, B, w, segs, out, tid - RT);
+}
+
+template <int RT, int QMAX>
+__device__ __forceinline__ bool dispatch_split(uint32_t nq, const GenCtx &g, uint32_t *buf, uint32_t B,
+                                               const DevWork &w, const DevSeg *segs, uint32_t *out, uint32_t *st)
+{
+    if (nq == (uint32_t)QMAX) {
+        run_item_split<RT, QMAX>(g, buf, B, w, segs, out, st);
+        return true;
+    }
+    if constexpr (QMAX > 1)
+        return dispatch_split<RT, QMAX - 1>(nq, g, buf, B, w, segs, out, st);
+    else
+        return false;
+}
+
+// Warp-specialised generation kernel: blocks of 2 RT threads.
+template <int RT, int QMAX>
+__global__ void __launch_bounds__(2 * RT, (2 * RT) >= 512 ? 1 : 512 / (2 * RT)) k_split(const LaunchArgs a)
+{
+    extern __shared__ __align__(16) uint32_t buf[];
+    __shared__ uint32_t s_item;
+    constexpr uint32_t T = 2u * RT;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
+    const uint32_t B = a.buf_words;
+    uint32_t item = blockIdx.x;
+    for (;;) {
+        if (a.persistent) {
+            if (tid == 0) s_item = atomicAdd(a.counter, 1u);
+            __syncthreads();
+            item = s_item;
+        }
+        if (item >= a.nwork) break;
+        const DevWork w = a.work[item];
+        DevGen &gd = a.gens[w.gen];
+        GenCtx g;
+        g.N = gd.N;
+        g.M = gd.M;
+        g.mask = gd.mask;
+        g.sh1 = gd.sh1;
+        g.sh2 = gd.sh2;
+        g.S = g.N - g.M;
+        g.rec_r = gd.rec[lane & 15u];
+        g.tmp_r = gd.tmp[lane & 15u];
+        const uint32_t nq = (g.S + RT - 1u) / RT;
+        bool ok = nq <= (uint32_t)QMAX && 2u * g.N + nq * RT + 32u <= B;
+        if (ok) {
+            uint32_t *st = a.state + gd.state_off;
+            for (uint32_t j = tid; j < g.N; j += T) buf[j] = st[j];
+            __syncthreads();
+            ok = dispatch_split<RT, QMAX>(nq, g, buf, B, w, a.segs + w.seg_begin, a.out, st);
+            if (ok && tid == 0) gd.count += w.total;
+        }
+        if (!ok && tid == 0) atomicOr(a.err, kErrBuffer);
+        __syncthreads();                                     // buffer and s_item reuse
+        if (!a.persistent) break;
+    }
+}
+
 template <int T, int QMAX>
 __global__ void __launch_bounds__(T, QMAX <= 6 ? 512 / T : (T >= 256 ? 1 : 256 / T)) k_generate(const LaunchArgs a)
 {

@@ -72,15 +72,22 @@ GenKernel gen_kernel_t64(uint32_t qmax);
 GenKernel gen_kernel_t128(uint32_t qmax);
 GenKernel gen_kernel_t256(uint32_t qmax);
 GenKernel gen_kernel_t512(uint32_t qmax);
+// Warp-specialised kernels: blocks of 2 RT threads (RT recursion + RT output).
+GenKernel split_kernel_rt64(uint32_t qmax);
+GenKernel split_kernel_rt128(uint32_t qmax);
+GenKernel split_kernel_rt256(uint32_t qmax);
+GenKernel split_kernel_rt512(uint32_t qmax);
 
-bool threads_supported(uint32_t threads);
-// Smallest compiled QMAX >= nq for this block size, 0 if none.
-uint32_t kernel_slots(uint32_t threads, uint32_t nq);
+bool threads_supported(uint32_t threads, uint32_t split);
+// Smallest compiled QMAX >= nq for this block size (and form), 0 if none.
+// For the split form a thread owns ceil(S / (threads / 2)) columns.
+uint32_t kernel_slots(uint32_t threads, uint32_t split, uint32_t nq);
 cudaError_t launch_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
                         const uint64_t *seeds, uint32_t first, uint32_t count, cudaStream_t s);
-cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t qmax, uint32_t grid,
+cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t split, uint32_t qmax, uint32_t grid,
                             cudaStream_t s);
-cudaError_t generate_occupancy(uint32_t threads, uint32_t qmax, uint32_t buf_words, int *blocks_per_sm);
+cudaError_t generate_occupancy(uint32_t threads, uint32_t split, uint32_t qmax, uint32_t buf_words,
+                               int *blocks_per_sm);
 cudaError_t launch_fill(uint32_t *buf, uint64_t words, uint32_t pattern, cudaStream_t s);
 
 }  // namespace mtgp

@@ -51,8 +51,17 @@ __global__ void k_fill(uint4 *buf, uint64_t n16, uint32_t pattern)
     }
 }
 
-GenKernel pick(uint32_t threads, uint32_t qmax)
+GenKernel pick(uint32_t threads, uint32_t split, uint32_t qmax)
 {
+    if (split) {
+        switch (threads) {
+        case 128: return split_kernel_rt64(qmax);
+        case 256: return split_kernel_rt128(qmax);
+        case 512: return split_kernel_rt256(qmax);
+        case 1024: return split_kernel_rt512(qmax);
+        default: return nullptr;
+        }
+    }
     switch (threads) {
     case 32: return gen_kernel_t32(qmax);
     case 64: return gen_kernel_t64(qmax);
@@ -65,13 +74,19 @@ GenKernel pick(uint32_t threads, uint32_t qmax)
 
 }  // namespace
 
-bool threads_supported(uint32_t threads) { return max_slots(threads) != 0u; }
-
-uint32_t kernel_slots(uint32_t threads, uint32_t nq)
+bool threads_supported(uint32_t threads, uint32_t split)
 {
     static const uint32_t compiled[] = {MTGP_QMAX_LIST};
     for (uint32_t q : compiled)
-        if (q >= nq && pick(threads, q)) return q;
+        if (pick(threads, split, q)) return true;
+    return false;
+}
+
+uint32_t kernel_slots(uint32_t threads, uint32_t split, uint32_t nq)
+{
+    static const uint32_t compiled[] = {MTGP_QMAX_LIST};
+    for (uint32_t q : compiled)
+        if (q >= nq && pick(threads, split, q)) return q;
     return 0;
 }
 
@@ -83,10 +98,10 @@ cudaError_t launch_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
     return cudaGetLastError();
 }
 
-cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t qmax, uint32_t grid,
+cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t split, uint32_t qmax, uint32_t grid,
                             cudaStream_t s)
 {
-    GenKernel k = pick(threads, qmax);
+    GenKernel k = pick(threads, split, qmax);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = (size_t)a.buf_words * sizeof(uint32_t);
     if (smem > 48u * 1024u) {
@@ -97,9 +112,10 @@ cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t qmax
     return cudaGetLastError();
 }
 
-cudaError_t generate_occupancy(uint32_t threads, uint32_t qmax, uint32_t buf_words, int *blocks_per_sm)
+cudaError_t generate_occupancy(uint32_t threads, uint32_t split, uint32_t qmax, uint32_t buf_words,
+                               int *blocks_per_sm)
 {
-    GenKernel k = pick(threads, qmax);
+    GenKernel k = pick(threads, split, qmax);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = (size_t)buf_words * sizeof(uint32_t);
     if (smem > 48u * 1024u) {

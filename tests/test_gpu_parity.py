@@ -86,43 +86,54 @@ def _round_size(spec):
     return p.N - p.pos
 
 
-@pytest.mark.parametrize("threads", [32, 64, 128, 256, 512])
+FORMS = [(32, 0), (64, 0), (128, 0), (256, 0), (512, 0), (128, 1), (256, 1), (512, 1), (1024, 1)]
+
+
+def _owners(threads, split):
+    return threads // 2 if split else threads
+
+
+def _max_slots(threads, split):
+    from paper_1005_4973_gb300._lib import MAX_SLOTS, MAX_SLOTS_SPLIT
+    return (MAX_SLOTS_SPLIT if split else MAX_SLOTS)[threads]
+
+
+@pytest.mark.parametrize("form", FORMS, ids=lambda f: f"{f[0]}{'s' if f[1] else 'p'}")
 @pytest.mark.parametrize("persistent", [0, 1])
-def test_launch_shapes(threads, persistent):
-    from paper_1005_4973_gb300._lib import MAX_SLOTS
-    gens = [g for g in MIXED if _round_size(g) <= threads * MAX_SLOTS[threads]]
+def test_launch_shapes(form, persistent):
+    threads, split = form
+    gens = [g for g in MIXED if _round_size(g) <= _owners(threads, split) * _max_slots(threads, split)]
     reqs, off = [], 0
     for g in range(len(gens)):
         for k, n in enumerate(RAGGED[g % 3::3] + [RAGGED[(g + 1) % len(RAGGED)]]):
             reqs.append((g, (g + k) % 3, n, off))
             off += n
-    pool, out = _run(gens, reqs, config=dict(threads=threads, persistent=persistent))
+    pool, out = _run(gens, reqs, config=dict(threads=threads, split=split, persistent=persistent))
     _check_blocked(gens, reqs, out, pool)
 
 
-@pytest.mark.parametrize("threads", [32, 64, 128, 256, 512])
-def test_every_slot_count(threads):
+@pytest.mark.parametrize("form", FORMS, ids=lambda f: f"{f[0]}{'s' if f[1] else 'p'}")
+def test_every_slot_count(form):
     """Generators whose round size S = N - M needs each slot count 1 .. max:
-    reduced-exponent and synthetic sets with M chosen to hit S = T q and
-    S = T q - 31 (fullest and emptiest last slot)."""
+    synthetic sets with M chosen to hit S = owners q and S = owners q - 31
+    (fullest and emptiest last slot)."""
     import paper_1005_4973_gb300 as M
-    from paper_1005_4973_gb300._lib import MAX_SLOTS
+    threads, split = form
+    owners = _owners(threads, split)
     ps, ops, n = [], [], 3001
-    for q in range(1, MAX_SLOTS[threads] + 1):
-        for S in {threads * q, max(1, threads * q - 31)}:
-            # smallest exponent whose N leaves room for M >= 2 with N - M = S
+    for q in range(1, _max_slots(threads, split) + 1):
+        for S in sorted({owners * q, max(1, owners * q - 31)}):
             N = S + 2 + (q % 5)
             mexp = 32 * N - 17
             if N > 4096:
                 continue
             lp = M.mtgp_params_draw(mexp, q, q)
             o = O.params_draw(mexp, q, q)
-            Mpos = N - S
-            lp.pos = Mpos
-            ops.append(O.params_from_fields(mexp, Mpos, o.sh1, o.sh2, q, list(o.R), list(o.T)))
+            lp.pos = N - S
+            ops.append(O.params_from_fields(mexp, N - S, o.sh1, o.sh2, q, list(o.R), list(o.T)))
             ps.append(lp)
     pool = M.Pool(ps, list(range(len(ps))), [11] * len(ps))
-    pool.set_config(threads=threads)
+    pool.set_config(threads=threads, split=split)
     out = torch.zeros(n * len(ps), dtype=torch.int32, device="cuda")
     pool.generate([(i, i % 3, n, i * n) for i in range(len(ps))], out)
     o = as_u32(out)
@@ -133,13 +144,18 @@ def test_every_slot_count(threads):
 
 
 @pytest.mark.parametrize("extra", [0, 1, 7, 300, 2000])
-def test_small_buffers_force_compaction(extra):
-    # buffer_words = 2N + T ceil(S/T) + 32 + extra: compaction every round or two
+@pytest.mark.parametrize("form", [(128, 0), (256, 1)], ids=["128p", "256s"])
+def test_small_buffers_force_compaction(extra, form):
+    # buffer_words = 2N + owners ceil(S/owners) + 32 + extra: compaction every
+    # round or two (in the split form every compaction drains the hand-off ring)
+    threads, split = form
+    owners = _owners(threads, split)
     gens = MIXED[:3]
     ps = [oracle_params(g) for g in gens]
-    need = max(2 * p.N + -(-(p.N - p.pos) // 128) * 128 + 32 for p in ps)
+    need = max(2 * p.N + -(-(p.N - p.pos) // owners) * owners + 32 for p in ps)
     reqs = [(g, g % 3, 20011, 20011 * g) for g in range(3)]
-    pool, out = _run(gens, reqs, config=dict(threads=128, buffer_words=need + extra))
+    reqs += [(g, (g + 1) % 3, 777, 60033 + 777 * g) for g in range(3)]
+    pool, out = _run(gens, reqs, config=dict(threads=threads, split=split, buffer_words=need + extra))
     _check_blocked(gens, reqs, out, pool)
 
 

@@ -104,7 +104,7 @@ cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t spli
     GenKernel k = pick(threads, split, qmax);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = (size_t)a.buf_words * sizeof(uint32_t);
-    if (smem > 48u * 1024u) {
+    if (smem + 1024u > 48u * 1024u) {     // dynamic + the kernels' static words past the default
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
@@ -118,7 +118,7 @@ cudaError_t generate_occupancy(uint32_t threads, uint32_t split, uint32_t qmax, 
     GenKernel k = pick(threads, split, qmax);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = (size_t)buf_words * sizeof(uint32_t);
-    if (smem > 48u * 1024u) {
+    if (smem + 1024u > 48u * 1024u) {     // dynamic + the kernels' static words past the default
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }

@@ -255,6 +255,43 @@ void mtgp_pool_destroy(mtgp_pool *p);
 mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_scratch,
                           void *stream, mtgp_config *best, float *best_ms);
 
+/* ---- allocation-free form ---------------------------------------------------
+ *
+ * The paper has no counterpart to this call.  It exists for callers that must
+ * not allocate device memory: code running inside a framework whose own
+ * allocator already reserves the device's memory, latency-sensitive loops
+ * (cudaMalloc and cudaFree can synchronise the whole device), and callers
+ * under a fixed memory budget.  Such callers own every buffer and pass it in.
+ *
+ * Generates, in one launch on `stream`, the requests reqs[0 .. nreq) for the
+ * `count` generators with parameter sets ps[0 .. count), blocked layout only
+ * (request j writes dev_out[out_offset .. out_offset + n), dtype as in
+ * mtgp_request).  Generator i's state is the N_i words at
+ * dev_states + state_offsets[i] (x_k .. x_{k+N-1}, oldest first; for example
+ * copied from mtgp_pool_read_state); it is read and advanced in place, so
+ * the next call continues the streams.  dev_states and dev_out are
+ * caller-owned, 4-byte aligned device buffers.
+ *
+ * Nothing is allocated: the per-call records (parameter tables, work list,
+ * error word) go to one file-scope device array of
+ * MTGP_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library keeps
+ * until the process exits.  count > MTGP_NOALLOC_MAX_GENS or
+ * nreq > MTGP_NOALLOC_MAX_REQS returns MTGP_EINVAL with a message.  The first
+ * call on each device looks up that array's device address (a one-time
+ * set-up); make that first call before any stream capture.  Every call
+ * shares the array and overwrites it (its control words are cleared on each
+ * call), so calls that overlap on the GPU -- on different streams, or from
+ * several host threads -- race; order them on one stream.  The records are
+ * copied from ordinary host memory, so the call waits for work already
+ * queued on `stream` before it returns.
+ */
+#define MTGP_NOALLOC_SCRATCH_BYTES 32768u
+#define MTGP_NOALLOC_MAX_GENS 64u
+#define MTGP_NOALLOC_MAX_REQS 64u
+mtgp_status mtgp_generate_noalloc(const mtgp_params *ps, uint32_t count, uint32_t *dev_states,
+                                  const uint64_t *state_offsets, const mtgp_request *reqs, uint32_t nreq,
+                                  void *dev_out, void *stream);
+
 /* ---- measurement helper --------------------------------------------------- */
 
 /*

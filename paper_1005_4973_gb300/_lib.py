@@ -18,6 +18,7 @@ MTGP_OK, MTGP_EINVAL, MTGP_ENOMEM, MTGP_ECUDA, MTGP_ETIMEOUT, MTGP_EBUSY = range
 MTGP_U32, MTGP_F32_12, MTGP_F32_01 = 0, 1, 2
 MTGP_LAYOUT_BLOCKED, MTGP_LAYOUT_INTERLEAVED = 0, 1
 MTGP_MAX_N = 4096
+MTGP_NOALLOC_SCRATCH_BYTES, MTGP_NOALLOC_MAX_GENS, MTGP_NOALLOC_MAX_REQS = 32768, 64, 64
 # block sizes compiled into the library and the column slots per thread each
 # supports (mirrors max_slots in the CUDA sources)
 MAX_SLOTS = {32: 11, 64: 12, 128: 11, 256: 6, 512: 8}
@@ -78,6 +79,8 @@ _SIGS = {
     "mtgp_autotune": (ctypes.c_int, [_vp, _P(mtgp_request), _u32, _vp, _vp, _P(mtgp_config),
                                      _P(ctypes.c_float)]),
     "mtgp_fill_probe": (ctypes.c_int, [_vp, _u64, _u32, _vp]),
+    "mtgp_generate_noalloc": (ctypes.c_int, [_P(mtgp_params), _u32, _vp, _P(_u64), _P(mtgp_request), _u32,
+                                             _vp, _vp]),
 }
 
 

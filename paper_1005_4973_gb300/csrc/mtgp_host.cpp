@@ -28,6 +28,18 @@ mtgp_status fail(mtgp_status st, const char *fmt, ...)
     return st;
 }
 
+}  // namespace
+
+namespace mtgp {
+int report_error(int status, const char *msg)
+{
+    g_err = msg;
+    return status;
+}
+}  // namespace mtgp
+
+namespace {
+
 mtgp_status cuda_fail(cudaError_t e, const char *what)
 {
     if (e == cudaErrorMemoryAllocation)

@@ -78,6 +78,9 @@ GenKernel split_kernel_rt128(uint32_t qmax);
 GenKernel split_kernel_rt256(uint32_t qmax);
 GenKernel split_kernel_rt512(uint32_t qmax);
 
+// Records msg as the calling thread's last error and returns status.
+int report_error(int status, const char *msg);
+
 bool threads_supported(uint32_t threads, uint32_t split);
 // Smallest compiled QMAX >= nq for this block size (and form), 0 if none.
 // For the split form a thread owns ceil(S / (threads / 2)) columns.

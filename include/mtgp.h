@@ -98,7 +98,8 @@ typedef struct mtgp_request {
 typedef struct mtgp_config {
     uint32_t threads;          /* threads per block: plain 32, 64, 128, 256, 512
                                   (at most 11, 12, 11, 6, 8 columns per thread);
-                                  split 128, 256, 512, 1024 (at most 12, 11, 6, 3) */
+                                  split 128, 256, 512, 1024 (at most 12, 11, 6, 3);
+                                  flow 128, 256, 512, 1024 (at most 12, 11, 6, 8)   */
     uint32_t persistent;       /* 1: grid of SMs x blocks_per_sm blocks taking work
                                   items longest first from a device counter;
                                   0: one block per work item                         */
@@ -107,7 +108,10 @@ typedef struct mtgp_config {
     uint32_t buffer_words;     /* shared-memory words per block, 0 = sized from the
                                   launch (>= 2N + owners ceil(S / owners) + 32 is
                                   required, owners = threads or threads / 2)         */
-    uint32_t split;            /* 0 plain form, 1 split (warp-specialised) form      */
+    uint32_t form;             /* 0 plain, 1 split (recursion and output warp groups
+                                  handing rounds over through named barriers),
+                                  2 flow (split groups, and each recursion warp
+                                  waits only for the warps holding its inputs)       */
 } mtgp_config;
 
 /* ---- library ------------------------------------------------------------ */

@@ -24,6 +24,8 @@ MTGP_NOALLOC_SCRATCH_BYTES, MTGP_NOALLOC_MAX_GENS, MTGP_NOALLOC_MAX_REQS = 32768
 MAX_SLOTS = {32: 11, 64: 12, 128: 11, 256: 6, 512: 8}
 # split form: block size -> columns per recursion thread (threads / 2 own columns)
 MAX_SLOTS_SPLIT = {128: 12, 256: 11, 512: 6, 1024: 3}
+# flow form: block size -> chunks of 32 columns per recursion warp (threads / 2 own columns)
+MAX_SLOTS_FLOW = {128: 12, 256: 11, 512: 6, 1024: 8}
 STATUS_NAMES = {0: "MTGP_OK", 1: "MTGP_EINVAL", 2: "MTGP_ENOMEM", 3: "MTGP_ECUDA",
                 4: "MTGP_ETIMEOUT", 5: "MTGP_EBUSY"}
 
@@ -46,7 +48,7 @@ class mtgp_request(ctypes.Structure):
 
 class mtgp_config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
-                ("threads", "persistent", "blocks_per_sm", "chunk", "buffer_words", "split")]
+                ("threads", "persistent", "blocks_per_sm", "chunk", "buffer_words", "form")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

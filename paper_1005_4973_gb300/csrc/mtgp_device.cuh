@@ -594,5 +594,333 @@ __global__ void __launch_bounds__(T, QMAX <= 6 ? 512 / T : (T >= 256 ? 1 : 256 /
     }
 }
 
+// ---------------------------------------------------------------------------
+// Flow form.  Same two groups as the split form (blocks of 2 W warps: W
+// recursion warps, W output warps), but without a barrier per round.  Round r,
+// column c reads x_{rS+c} and x_{rS+c+1}, i.e. columns c-M and c-M+1 of round
+// r-1 (of round r-2 when c < M, Sec. 3.2), and its own output of round r-1.
+// Recursion warp w owns the 32 C consecutive columns [32 C w, 32 C (w+1)) and,
+// before round r, waits only until the warps holding those input columns have
+// published round r-1 (or r-2) in a per-warp progress counter in shared
+// memory; it publishes its own counter with a release store after the round.
+// Output warp w waits for recursion warp w's round r and for the column to its
+// left of round r-1 (the tempering word x_{M-1+i}, Sec. 3.7), then tempers,
+// converts and stores.  The recursion warps never store to global memory, so
+// their release stores do not wait on HBM writes.  A block barrier is taken
+// only every E rounds, when the buffer is compacted, and at the end of a work
+// item.  Every wait is bounded: after kSpinLimit polls the warp records
+// kErrTimeout and stops waiting (results are then invalid, the kernel still
+// ends).
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t ld_acquire_shared(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.cta.shared.b32 %0, [%1];"
+                 : "=r"(v)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p))
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_shared(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v)
+                 : "memory");
+}
+
+// Waits (warp-uniformly) until *ctr >= need.  `failed` turns every later wait
+// of this warp into a no-op once one has run out.
+__device__ __forceinline__ void wait_progress(const uint32_t *ctr, uint32_t need, bool &failed, unsigned *err)
+{
+    if (failed) return;
+    uint32_t spins = 0;
+    while (ld_acquire_shared(ctr) < need) {
+        if (++spins > kSpinLimit) {
+            failed = true;
+            if ((threadIdx.x & 31u) == 0) atomicOr(err, kErrTimeout);
+            return;
+        }
+    }
+}
+
+// Input dependencies of one recursion warp: up to two ranges of warps, each
+// at a fixed round offset d (the warps must have published round r - d).
+struct FlowDeps {
+    uint32_t lo[2], hi[2], d[2];
+    uint32_t n;
+};
+
+// Dependencies of recursion warp w owning columns [lo, hi] of rounds of S
+// words, with `active` warps of `span` columns each (Sec. 3.2 indices).
+__device__ __forceinline__ FlowDeps flow_deps(uint32_t w, uint32_t lo, uint32_t hi, uint32_t S, uint32_t M,
+                                              uint32_t active, uint32_t span)
+{
+    FlowDeps f;
+    f.n = 0;
+    if (M > S) {                                   // inputs may lie several rounds back:
+        f.lo[0] = 0;                               // wait for every warp's round r-1
+        f.hi[0] = active - 1u;
+        f.d[0] = 1;
+        f.n = 1;
+        return f;
+    }
+    const int a = (int)lo - (int)M, b = (int)hi - (int)M + 1;
+    if (b >= 0) {                                  // columns [max(a,0), b] of round r-1
+        f.lo[f.n] = (uint32_t)(a > 0 ? a : 0) / span;
+        f.hi[f.n] = (uint32_t)b / span;
+        f.d[f.n] = 1;
+        ++f.n;
+    }
+    if (a < 0) {                                   // columns [a+S, min(b,-1)+S] of round r-2
+        f.lo[f.n] = (uint32_t)(a + (int)S) / span;
+        f.hi[f.n] = (uint32_t)((b < 0 ? b : -1) + (int)S) / span;
+        f.d[f.n] = 2;
+        ++f.n;
+    }
+    (void)w;
+    return f;
+}
+
+// Recursion warp w: rounds [r0, re) of an epoch whose first round starts at
+// buffer position rel0.  prev holds x_{N+(r-1)S+c} for each owned column.
+template <int C>
+__device__ __forceinline__ void flow_recursion(const GenCtx &g, uint32_t *buf, uint32_t rel0, uint32_t r0,
+                                               uint32_t re, uint64_t total, uint32_t w, uint32_t lane,
+                                               const FlowDeps &dep, uint32_t (&prev)[C], uint32_t *prog,
+                                               bool &failed, unsigned *err)
+{
+    const uint32_t base = 32u * C * w + lane;       // column of chunk 0
+    for (uint32_t r = r0; r < re; ++r) {
+        const uint64_t k0 = (uint64_t)r * g.S;
+        const uint32_t S_r = (uint32_t)min((uint64_t)g.S, total - k0);
+        for (uint32_t i = 0; i < dep.n; ++i) {
+            if (r < dep.d[i]) continue;
+            const uint32_t need = r - dep.d[i] + 1u;
+            for (uint32_t v = dep.lo[i]; v <= dep.hi[i]; ++v)
+                if (v != w) wait_progress(prog + v, need, failed, err);
+        }
+        const uint32_t *x = buf + rel0 + (r - r0) * g.S + base;
+        uint32_t *xn_p = buf + rel0 + (r - r0) * g.S + base + g.N;
+        uint32_t a[C], b[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            a[j] = x[32 * j];
+            b[j] = x[32 * j + 1];
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const uint32_t t = b[j] ^ (a[j] & g.mask);
+            a[j] = t ^ (t << g.sh1) ^ (prev[j] >> g.sh2);
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const uint32_t xn = a[j] ^ __shfl_sync(0xffffffffu, g.rec_r, (int)a[j], 16);
+            if (base + 32u * j < S_r) xn_p[32 * j] = xn;
+            prev[j] = xn;
+        }
+        __syncwarp();
+        st_release_shared(prog + w, r + 1u);
+    }
+}
+
+// Output routing of one work item, carried by each output warp: the segment
+// holding word index k and that segment's fields.
+struct SegCursor {
+    const DevSeg *segs;
+    uint32_t si, nseg;
+    uint64_t start, end;
+    DevSeg cur;
+};
+
+// Advances to the segment holding word k (k below the item's total; the
+// cursor never moves past the item's last segment).
+__device__ __forceinline__ void seg_seek(SegCursor &sc, uint64_t k)
+{
+    while (k >= sc.end && sc.si + 1u < sc.nseg) {
+        ++sc.si;
+        sc.start = sc.end;
+        sc.cur = sc.segs[sc.si];
+        sc.end += sc.cur.n;
+    }
+}
+
+// Output warp w: rounds [r0, re) of an epoch (same positions as the
+// recursion warps).  Tempering (Sec. 3.7), conversion (Sec. 6), store.
+template <int C>
+__device__ __forceinline__ void flow_output(const GenCtx &g, const uint32_t *buf, uint32_t rel0, uint32_t r0,
+                                            uint32_t re, uint64_t total, uint32_t w, uint32_t lane,
+                                            uint32_t active, const uint32_t *prog, SegCursor &sc,
+                                            uint32_t *out_base, bool &failed, unsigned *err)
+{
+    const uint32_t lo = 32u * C * w, base = lo + lane;
+    const uint32_t hi = min(lo + 32u * C, g.S) - 1u;
+    for (uint32_t r = r0; r < re; ++r) {
+        const uint64_t k0 = (uint64_t)r * g.S;
+        const uint32_t S_r = (uint32_t)min((uint64_t)g.S, total - k0);
+        if (lo >= S_r) continue;                                      // no column of this warp in the round
+        wait_progress(prog + w, r + 1u, failed, err);                  // x_{N+i} of round r
+        if (lo > 0)                                                   // x_{M-1+i} of column lo-1
+            wait_progress(prog + (lo - 1u) / (32u * C), r, failed, err);
+        else if (r >= 2)
+            wait_progress(prog + active - 1u, r - 1u, failed, err);
+        const uint32_t *x = buf + rel0 + (r - r0) * g.S + base;
+        uint32_t xn[C], xt[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            xn[j] = x[g.N + 32 * j];
+            xt[j] = x[g.M - 1u + 32 * j];
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            uint32_t s = xt[j] ^ (xt[j] >> 16);
+            s ^= s >> 8;
+            xn[j] ^= __shfl_sync(0xffffffffu, g.tmp_r, (int)s, 16);
+        }
+        const uint64_t kf = k0 + lo, kl = k0 + min(hi, S_r - 1u);
+        seg_seek(sc, kf);
+        if (kl < sc.end && sc.cur.chunk_log2 == kBlocked) {           // whole warp in one segment
+            uint32_t *o = out_base + sc.cur.out_off + (kf - sc.start) + lane;
+            const uint32_t dt = sc.cur.dtype;
+#pragma unroll
+            for (int j = 0; j < C; ++j)
+                if (base + 32u * j < S_r) __stcs(o + 32 * j, finish(dt, xn[j]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                if (base + 32u * j >= S_r) continue;
+                const uint64_t k = k0 + base + 32u * j;
+                SegCursor t = sc;
+                seg_seek(t, k);
+                const uint64_t kk = k - t.start;
+                const uint64_t idx = t.cur.chunk_log2 == kBlocked
+                                         ? kk
+                                         : (kk >> t.cur.chunk_log2) * t.cur.stride +
+                                               (kk & ((1ull << t.cur.chunk_log2) - 1ull));
+                __stcs(out_base + t.cur.out_off + idx, finish(t.cur.dtype, xn[j]));
+            }
+        }
+    }
+}
+
+// All rounds of one work item in the flow form, C chunks of 32 columns per
+// recursion warp.  Epochs of E rounds between block barriers; at each epoch
+// end the N newest words move to the front of the buffer.
+template <int W, int C>
+__device__ __forceinline__ void run_item_flow(const GenCtx &g, uint32_t *buf, uint32_t B, const DevWork &w,
+                                              const DevSeg *segs, uint32_t *out, uint32_t *st, uint32_t *prog,
+                                              unsigned *err)
+{
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+    const uint32_t span = 32u * C;
+    const uint32_t active = (g.S + span - 1u) / span;
+    const bool is_rec = warp < (uint32_t)W;
+    const uint32_t wg = is_rec ? warp : warp - W;                     // warp index in its group
+    const bool working = wg < active;
+    const uint32_t rounds = (uint32_t)((w.total + g.S - 1u) / g.S);
+    const uint32_t margin = span + 32u;
+    uint32_t E = (B - g.N - margin) / g.S;
+    if (E < 1u) E = 1u;
+    bool failed = false;
+    uint32_t prev[C];
+    FlowDeps dep{};
+    if (is_rec && working) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) {                                  // x_{c+M}, c = column
+            const uint32_t c = wg * span + 32u * j + lane;
+            prev[j] = c < g.S ? buf[c + g.M] : 0u;
+        }
+        dep = flow_deps(wg, wg * span, min(wg * span + span, g.S) - 1u, g.S, g.M, active, span);
+    }
+    SegCursor sc;
+    sc.segs = segs;
+    sc.nseg = w.seg_count;
+    sc.si = 0;
+    sc.start = 0;
+    sc.cur = segs[0];
+    sc.end = sc.cur.n;
+    uint32_t rel = 0;
+    for (uint32_t r0 = 0; r0 < rounds; r0 += E) {
+        const uint32_t re = min(rounds, r0 + E);
+        if (working) {
+            if (is_rec)
+                flow_recursion<C>(g, buf, rel, r0, re, w.total, wg, lane, dep, prev, prog, failed, err);
+            else
+                flow_output<C>(g, buf, rel, r0, re, w.total, wg, lane, active, prog, sc, out, failed, err);
+        }
+        const uint32_t words = (uint32_t)(min((uint64_t)re * g.S, w.total) - (uint64_t)r0 * g.S);
+        __syncthreads();
+        if (re < rounds) {                                              // compaction (words >= N)
+            for (uint32_t j = tid; j < g.N; j += 64u * W) buf[j] = buf[rel + words + j];
+            __syncthreads();
+            rel = 0;
+        } else {
+            rel += words;
+        }
+    }
+    for (uint32_t j = tid; j < g.N; j += 64u * W) st[j] = buf[rel + j];   // state write-back (Sec. 8)
+}
+
+template <int W, int CMAX>
+__device__ __forceinline__ bool dispatch_flow(uint32_t nc, const GenCtx &g, uint32_t *buf, uint32_t B,
+                                              const DevWork &w, const DevSeg *segs, uint32_t *out, uint32_t *st,
+                                              uint32_t *prog, unsigned *err)
+{
+    if (nc == (uint32_t)CMAX) {
+        run_item_flow<W, CMAX>(g, buf, B, w, segs, out, st, prog, err);
+        return true;
+    }
+    if constexpr (CMAX > 1)
+        return dispatch_flow<W, CMAX - 1>(nc, g, buf, B, w, segs, out, st, prog, err);
+    else
+        return false;
+}
+
+// Flow-form generation kernel: blocks of 2 W warps (64 W threads).
+template <int W, int CMAX>
+__global__ void __launch_bounds__(64 * W, (64 * W) >= 512 ? 1 : 512 / (64 * W)) k_flow(const LaunchArgs a)
+{
+    extern __shared__ __align__(16) uint32_t buf[];
+    __shared__ uint32_t s_item;
+    __shared__ uint32_t prog[W];
+    constexpr uint32_t T = 64u * W;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
+    const uint32_t B = a.buf_words;
+    uint32_t item = blockIdx.x;
+    for (;;) {
+        if (a.persistent) {
+            if (tid == 0) s_item = atomicAdd(a.counter, 1u);
+            __syncthreads();
+            item = s_item;
+        }
+        if (item >= a.nwork) break;
+        const DevWork w = a.work[item];
+        DevGen &gd = a.gens[w.gen];
+        GenCtx g;
+        g.N = gd.N;
+        g.M = gd.M;
+        g.mask = gd.mask;
+        g.sh1 = gd.sh1;
+        g.sh2 = gd.sh2;
+        g.S = g.N - g.M;
+        g.rec_r = gd.rec[lane & 15u];
+        g.tmp_r = gd.tmp[lane & 15u];
+        const uint32_t nc = (g.S + 32u * W - 1u) / (32u * W);          // chunks per recursion warp
+        const uint32_t span = 32u * nc;
+        bool ok = nc <= (uint32_t)CMAX && 2u * g.N + 2u * g.S + span + 32u <= B;
+        if (ok) {
+            uint32_t *st = a.state + gd.state_off;
+            for (uint32_t j = tid; j < g.N; j += T) buf[j] = st[j];
+            if (tid < (uint32_t)W) prog[tid] = 0u;
+            __syncthreads();
+            ok = dispatch_flow<W, CMAX>(nc, g, buf, B, w, a.segs + w.seg_begin, a.out, st, prog, a.err);
+            if (ok && tid == 0) gd.count += w.total;
+        }
+        if (!ok && tid == 0) atomicOr(a.err, kErrBuffer);
+        __syncthreads();                                     // buffer, counters and s_item reuse
+        if (!a.persistent) break;
+    }
+}
+
 }  // namespace dev
 }  // namespace mtgp

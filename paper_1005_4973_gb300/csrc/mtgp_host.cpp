@@ -181,11 +181,9 @@ const mtgp_config kDefaultConfig = {128u, 0u, 0u, 256u, 0u, 0u};
 
 mtgp_status check_config(const mtgp_config &c)
 {
-    if (c.split > 1u) return fail(MTGP_EINVAL, "split must be 0 or 1");
-    if (!threads_supported(c.threads, c.split))
-        return fail(MTGP_EINVAL, c.split ? "split blocks must have 128, 256, 512 or 1024 threads, got %u"
-                                         : "threads must be 32, 64, 128, 256 or 512, got %u",
-                    c.threads);
+    if (c.form > 2u) return fail(MTGP_EINVAL, "form must be 0 (plain), 1 (split) or 2 (flow)");
+    if (!threads_supported(c.threads, c.form))
+        return fail(MTGP_EINVAL, "no kernel of form %u with %u threads per block", c.form, c.threads);
     if (c.persistent > 1u) return fail(MTGP_EINVAL, "persistent must be 0 or 1");
     if (c.blocks_per_sm > 32u) return fail(MTGP_EINVAL, "blocks_per_sm must be <= 32");
     if (c.chunk < 32u || (c.chunk & (c.chunk - 1u)))
@@ -319,19 +317,22 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
         nmax = std::max(nmax, g.N);
         smax = std::max(smax, g.N - g.M);
     }
-    const uint32_t owners = c.split ? c.threads / 2u : c.threads;   // threads owning columns
-    const uint32_t qmax = kernel_slots(c.threads, c.split, (smax + owners - 1u) / owners);
+    const uint32_t owners = c.form ? c.threads / 2u : c.threads;   // threads owning columns
+    const uint32_t qmax = kernel_slots(c.threads, c.form, (smax + owners - 1u) / owners);
     if (!qmax)
-        return fail(MTGP_EINVAL, "no compiled kernel runs rounds of %u words with %u threads (split %u)", smax,
-                    c.threads, c.split);
+        return fail(MTGP_EINVAL, "no compiled kernel runs rounds of %u words with %u threads (form %u)", smax,
+                    c.threads, c.form);
     // shared buffer: at least 2N + T ceil(S/T) + 32 words (reads of the last
     // column slot stay inside, compaction never overlaps); up to 32 rounds
     // between compactions if the blocks wanted per SM fit
     uint32_t need = 0;
     for (const DevWork &w : plan.work) {
         const DevGen &g = p->host_gens[w.gen];
-        const uint32_t S = g.N - g.M, span = (S + owners - 1u) / owners * owners;
-        need = std::max(need, 2u * g.N + span + 32u);
+        const uint32_t S = g.N - g.M, nq = (S + owners - 1u) / owners;
+        if (c.form == 2u)   // flow: epochs of at least N + S words between compactions
+            need = std::max(need, 2u * g.N + 2u * S + 32u * nq + 32u);
+        else                // plain / split: reads of the last column slot stay inside
+            need = std::max(need, 2u * g.N + nq * owners + 32u);
     }
     uint32_t B = c.buffer_words;
     if (!B) {
@@ -360,7 +361,7 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     if (c.persistent) {
         CU(cudaMemsetAsync(p->d_ctl, 0, sizeof(unsigned), s), "reset work counter");
         int occ = 0;
-        CU(generate_occupancy(c.threads, c.split, qmax, B, &occ), "occupancy");
+        CU(generate_occupancy(c.threads, c.form, qmax, B, &occ), "occupancy");
         if (occ < 1) return fail(MTGP_EINVAL, "configuration does not fit on an SM");
         const int per_sm = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, occ) : occ;
         grid = std::min<uint32_t>(grid, (uint32_t)(per_sm * p->sm_count));
@@ -376,7 +377,7 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     a.nwork = (uint32_t)plan.work.size();
     a.buf_words = B;
     a.persistent = c.persistent;
-    CU(launch_generate(a, c.threads, c.split, qmax, grid, s), "generate kernel launch");
+    CU(launch_generate(a, c.threads, c.form, qmax, grid, s), "generate kernel launch");
     CU(cudaEventRecord(p->ev_done, s), "cudaEventRecord");
     p->last_stream = s;
     p->used = true;
@@ -822,13 +823,13 @@ mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
     if (st != MTGP_OK) return st;
     const mtgp_config orig = p->cfg;
     std::vector<mtgp_config> cands;
-    for (uint32_t split : {0u, 1u})
+    for (uint32_t form : {0u, 1u, 2u})
         for (uint32_t threads : {32u, 64u, 128u, 256u, 512u, 1024u})
             for (uint32_t pers : {0u, 1u})
                 for (uint32_t bps : {0u, 1u, 2u, 3u, 4u, 6u, 8u}) {
                     if (!pers && bps) continue;
-                    if (!threads_supported(threads, split)) continue;
-                    cands.push_back(mtgp_config{threads, pers, bps, orig.chunk, 0u, split});
+                    if (!threads_supported(threads, form)) continue;
+                    cands.push_back(mtgp_config{threads, pers, bps, orig.chunk, 0u, form});
                 }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0), "cudaEventCreate");

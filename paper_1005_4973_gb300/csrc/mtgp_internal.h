@@ -40,6 +40,7 @@ static_assert(sizeof(DevWork) == 32, "DevWork layout");
 
 // Error bits the kernels may set in LaunchArgs::err.
 constexpr unsigned kErrBuffer = 1u;  // a generator did not fit the launch's shape or buffer
+constexpr unsigned kErrTimeout = 2u; // a bounded wait between warps ran out
 
 struct LaunchArgs {
     DevGen *gens;
@@ -77,19 +78,24 @@ GenKernel split_kernel_rt64(uint32_t qmax);
 GenKernel split_kernel_rt128(uint32_t qmax);
 GenKernel split_kernel_rt256(uint32_t qmax);
 GenKernel split_kernel_rt512(uint32_t qmax);
+// Flow-form kernels: blocks of 2 W warps (W recursion + W output warps).
+GenKernel flow_kernel_w2(uint32_t cmax);
+GenKernel flow_kernel_w4(uint32_t cmax);
+GenKernel flow_kernel_w8(uint32_t cmax);
+GenKernel flow_kernel_w16(uint32_t cmax);
 
 // Records msg as the calling thread's last error and returns status.
 int report_error(int status, const char *msg);
 
-bool threads_supported(uint32_t threads, uint32_t split);
-// Smallest compiled QMAX >= nq for this block size (and form), 0 if none.
-// For the split form a thread owns ceil(S / (threads / 2)) columns.
-uint32_t kernel_slots(uint32_t threads, uint32_t split, uint32_t nq);
+bool threads_supported(uint32_t threads, uint32_t form);
+// Smallest compiled QMAX >= nq for this block size and form, 0 if none.
+// In the split and flow forms a thread owns ceil(S / (threads / 2)) columns.
+uint32_t kernel_slots(uint32_t threads, uint32_t form, uint32_t nq);
 cudaError_t launch_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
                         const uint64_t *seeds, uint32_t first, uint32_t count, cudaStream_t s);
-cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t split, uint32_t qmax, uint32_t grid,
+cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t form, uint32_t qmax, uint32_t grid,
                             cudaStream_t s);
-cudaError_t generate_occupancy(uint32_t threads, uint32_t split, uint32_t qmax, uint32_t buf_words,
+cudaError_t generate_occupancy(uint32_t threads, uint32_t form, uint32_t qmax, uint32_t buf_words,
                                int *blocks_per_sm);
 cudaError_t launch_fill(uint32_t *buf, uint64_t words, uint32_t pattern, cudaStream_t s);
 

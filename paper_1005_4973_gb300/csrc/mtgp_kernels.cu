@@ -51,9 +51,18 @@ __global__ void k_fill(uint4 *buf, uint64_t n16, uint32_t pattern)
     }
 }
 
-GenKernel pick(uint32_t threads, uint32_t split, uint32_t qmax)
+GenKernel pick(uint32_t threads, uint32_t form, uint32_t qmax)
 {
-    if (split) {
+    if (form == 2u) {
+        switch (threads) {
+        case 128: return flow_kernel_w2(qmax);
+        case 256: return flow_kernel_w4(qmax);
+        case 512: return flow_kernel_w8(qmax);
+        case 1024: return flow_kernel_w16(qmax);
+        default: return nullptr;
+        }
+    }
+    if (form == 1u) {
         switch (threads) {
         case 128: return split_kernel_rt64(qmax);
         case 256: return split_kernel_rt128(qmax);
@@ -74,19 +83,19 @@ GenKernel pick(uint32_t threads, uint32_t split, uint32_t qmax)
 
 }  // namespace
 
-bool threads_supported(uint32_t threads, uint32_t split)
+bool threads_supported(uint32_t threads, uint32_t form)
 {
     static const uint32_t compiled[] = {MTGP_QMAX_LIST};
     for (uint32_t q : compiled)
-        if (pick(threads, split, q)) return true;
+        if (pick(threads, form, q)) return true;
     return false;
 }
 
-uint32_t kernel_slots(uint32_t threads, uint32_t split, uint32_t nq)
+uint32_t kernel_slots(uint32_t threads, uint32_t form, uint32_t nq)
 {
     static const uint32_t compiled[] = {MTGP_QMAX_LIST};
     for (uint32_t q : compiled)
-        if (q >= nq && pick(threads, split, q)) return q;
+        if (q >= nq && pick(threads, form, q)) return q;
     return 0;
 }
 
@@ -98,10 +107,10 @@ cudaError_t launch_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
     return cudaGetLastError();
 }
 
-cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t split, uint32_t qmax, uint32_t grid,
+cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t form, uint32_t qmax, uint32_t grid,
                             cudaStream_t s)
 {
-    GenKernel k = pick(threads, split, qmax);
+    GenKernel k = pick(threads, form, qmax);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = (size_t)a.buf_words * sizeof(uint32_t);
     if (smem + 1024u > 48u * 1024u) {     // dynamic + the kernels' static words past the default
@@ -112,10 +121,10 @@ cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t spli
     return cudaGetLastError();
 }
 
-cudaError_t generate_occupancy(uint32_t threads, uint32_t split, uint32_t qmax, uint32_t buf_words,
+cudaError_t generate_occupancy(uint32_t threads, uint32_t form, uint32_t qmax, uint32_t buf_words,
                                int *blocks_per_sm)
 {
-    GenKernel k = pick(threads, split, qmax);
+    GenKernel k = pick(threads, form, qmax);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = (size_t)buf_words * sizeof(uint32_t);
     if (smem + 1024u > 48u * 1024u) {     // dynamic + the kernels' static words past the default

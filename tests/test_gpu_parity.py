@@ -86,42 +86,52 @@ def _round_size(spec):
     return p.N - p.pos
 
 
-FORMS = [(32, 0), (64, 0), (128, 0), (256, 0), (512, 0), (128, 1), (256, 1), (512, 1), (1024, 1)]
+FORMS = [(32, 0), (64, 0), (128, 0), (256, 0), (512, 0), (128, 1), (256, 1), (512, 1), (1024, 1),
+         (128, 2), (256, 2), (512, 2), (1024, 2)]
+FORM_ID = lambda f: f"{f[0]}{'psf'[f[1]]}"
 
 
-def _owners(threads, split):
-    return threads // 2 if split else threads
+def _need(p, threads, fm):
+    """Smallest buffer_words for parameter set p (see mtgp_config.buffer_words)."""
+    owners = _owners(threads, fm)
+    S = p.N - p.pos
+    nq = -(-S // owners)
+    return 2 * p.N + 2 * S + 32 * nq + 32 if fm == 2 else 2 * p.N + nq * owners + 32
 
 
-def _max_slots(threads, split):
-    from paper_1005_4973_gb300._lib import MAX_SLOTS, MAX_SLOTS_SPLIT
-    return (MAX_SLOTS_SPLIT if split else MAX_SLOTS)[threads]
+def _owners(threads, form):
+    return threads // 2 if form else threads
 
 
-@pytest.mark.parametrize("form", FORMS, ids=lambda f: f"{f[0]}{'s' if f[1] else 'p'}")
+def _max_slots(threads, form):
+    from paper_1005_4973_gb300._lib import MAX_SLOTS, MAX_SLOTS_FLOW, MAX_SLOTS_SPLIT
+    return (MAX_SLOTS_SPLIT if form == 1 else MAX_SLOTS_FLOW if form == 2 else MAX_SLOTS)[threads]
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_ID)
 @pytest.mark.parametrize("persistent", [0, 1])
 def test_launch_shapes(form, persistent):
-    threads, split = form
-    gens = [g for g in MIXED if _round_size(g) <= _owners(threads, split) * _max_slots(threads, split)]
+    threads, fm = form
+    gens = [g for g in MIXED if _round_size(g) <= _owners(threads, fm) * _max_slots(threads, fm)]
     reqs, off = [], 0
     for g in range(len(gens)):
         for k, n in enumerate(RAGGED[g % 3::3] + [RAGGED[(g + 1) % len(RAGGED)]]):
             reqs.append((g, (g + k) % 3, n, off))
             off += n
-    pool, out = _run(gens, reqs, config=dict(threads=threads, split=split, persistent=persistent))
+    pool, out = _run(gens, reqs, config=dict(threads=threads, form=fm, persistent=persistent))
     _check_blocked(gens, reqs, out, pool)
 
 
-@pytest.mark.parametrize("form", FORMS, ids=lambda f: f"{f[0]}{'s' if f[1] else 'p'}")
+@pytest.mark.parametrize("form", FORMS, ids=FORM_ID)
 def test_every_slot_count(form):
     """Generators whose round size S = N - M needs each slot count 1 .. max:
     synthetic sets with M chosen to hit S = owners q and S = owners q - 31
     (fullest and emptiest last slot)."""
     import paper_1005_4973_gb300 as M
-    threads, split = form
-    owners = _owners(threads, split)
+    threads, fm = form
+    owners = _owners(threads, fm)
     ps, ops, n = [], [], 3001
-    for q in range(1, _max_slots(threads, split) + 1):
+    for q in range(1, _max_slots(threads, fm) + 1):
         for S in sorted({owners * q, max(1, owners * q - 31)}):
             N = S + 2 + (q % 5)
             mexp = 32 * N - 17
@@ -133,7 +143,7 @@ def test_every_slot_count(form):
             ops.append(O.params_from_fields(mexp, N - S, o.sh1, o.sh2, q, list(o.R), list(o.T)))
             ps.append(lp)
     pool = M.Pool(ps, list(range(len(ps))), [11] * len(ps))
-    pool.set_config(threads=threads, split=split)
+    pool.set_config(threads=threads, form=fm)
     out = torch.zeros(n * len(ps), dtype=torch.int32, device="cuda")
     pool.generate([(i, i % 3, n, i * n) for i in range(len(ps))], out)
     o = as_u32(out)
@@ -143,19 +153,32 @@ def test_every_slot_count(form):
         assert np.array_equal(pool.read_state(i), st)
 
 
+@pytest.mark.parametrize("tail", [1, 5, 31, 33, 97])
+def test_flow_partial_last_round_with_idle_warps(tail):
+    # 1024-thread flow blocks give a 300-word round to ten 32-column warps; a
+    # final round of `tail` words leaves most of them without a column, and
+    # their output warps must neither route nor store anything for it
+    g = [WL.GenSpec(11213, 1, 0, 0)]
+    S = _round_size(g[0])
+    n1, n2 = 7 * S + tail, 3 * S + tail
+    reqs = [(0, 0, n1, 0), (0, 2, n2, n1)]
+    pool, out = _run(g, reqs, config=dict(threads=1024, form=2))
+    _check_blocked(g, reqs, out, pool)
+
+
 @pytest.mark.parametrize("extra", [0, 1, 7, 300, 2000])
-@pytest.mark.parametrize("form", [(128, 0), (256, 1)], ids=["128p", "256s"])
+@pytest.mark.parametrize("form", [(128, 0), (256, 1), (256, 2), (1024, 2)], ids=FORM_ID)
 def test_small_buffers_force_compaction(extra, form):
-    # buffer_words = 2N + owners ceil(S/owners) + 32 + extra: compaction every
-    # round or two (in the split form every compaction drains the hand-off ring)
-    threads, split = form
-    owners = _owners(threads, split)
+    # buffer_words at (or just above) its minimum: compaction every round or
+    # few rounds (split form: every compaction drains the hand-off ring; flow
+    # form: every epoch ends at a block barrier)
+    threads, fm = form
     gens = MIXED[:3]
     ps = [oracle_params(g) for g in gens]
-    need = max(2 * p.N + -(-(p.N - p.pos) // owners) * owners + 32 for p in ps)
+    need = max(_need(p, threads, fm) for p in ps)
     reqs = [(g, g % 3, 20011, 20011 * g) for g in range(3)]
     reqs += [(g, (g + 1) % 3, 777, 60033 + 777 * g) for g in range(3)]
-    pool, out = _run(gens, reqs, config=dict(threads=threads, split=split, buffer_words=need + extra))
+    pool, out = _run(gens, reqs, config=dict(threads=threads, form=fm, buffer_words=need + extra))
     _check_blocked(gens, reqs, out, pool)
 
 

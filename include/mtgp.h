@@ -259,6 +259,109 @@ void mtgp_pool_destroy(mtgp_pool *p);
 mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_scratch,
                           void *stream, mtgp_config *best, float *best_ms);
 
+/*
+ * Error word of the pool's last launches: bit 0 a generator did not fit the
+ * launch's kernel shape or shared buffer, bit 1 a bounded wait between warps
+ * ran out (flow form).  Synchronous; clears the word.  Outputs of a launch
+ * that set a bit are invalid.
+ */
+mtgp_status mtgp_pool_errors(mtgp_pool *p, uint32_t *flags);
+
+/* ---- graph-captured batched launch --------------------------------------------
+ *
+ * Batching across many generators (not in the paper, which launches once per
+ * call, Sec. 8): one persistent launch -- a grid of SMs x blocks_per_sm blocks
+ * pulling work items longest first -- is captured once into a CUDA graph whose
+ * work list, work-item count and output base live in a library-owned device
+ * buffer.  Each mtgp_graph_set_requests rewrites that buffer (one async copy
+ * on `stream`) and each mtgp_graph_launch replays the graph, so the launch
+ * cost stays constant however the requests change.
+ */
+typedef struct mtgp_graph mtgp_graph;
+
+/* Captures the launch for pool p with the pool's configuration (persistent),
+ * sized for every generator of the pool and at most max_items work items
+ * (distinct generators) and max_items segments per replay.  Synchronous.
+ * Errors: MTGP_EINVAL, MTGP_ENOMEM, MTGP_ECUDA. */
+mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mtgp_graph **out);
+
+/* Sets the requests of the next replays: same contract as mtgp_pool_generate
+ * (grouping, order, layouts, dev_out), stream-ordered on `stream`.  The work
+ * list stays in place for later replays until the next call. */
+mtgp_status mtgp_graph_set_requests(mtgp_graph *g, const mtgp_request *reqs, uint32_t nreq, void *dev_out,
+                                    mtgp_layout layout, void *stream);
+
+/* Replays the captured launch on `stream`: generates the current requests,
+ * each replay continuing the generators' streams. */
+mtgp_status mtgp_graph_launch(mtgp_graph *g, void *stream);
+
+/* Error word of the graph's launches (as mtgp_pool_errors).  Synchronous. */
+mtgp_status mtgp_graph_errors(mtgp_graph *g, uint32_t *flags);
+
+/* Frees the graph (after the pool's work finished). */
+void mtgp_graph_destroy(mtgp_graph *g);
+
+/* ---- continuous-batching server ----------------------------------------------
+ *
+ * Serving loop over a pool (not in the paper): requests (generator, dtype, n)
+ * arrive at any time; each mtgp_server_poll retires finished ticks, admits
+ * pending requests in submission order while a slot is free and the output
+ * fits in the server's device arena (admission by free memory), and launches
+ * one tick -- one replay of the pool's captured persistent launch
+ * (mtgp_graph_*) that advances every admitted request by up to `chunk`
+ * numbers.  Requests that arrive while others are on the GPU join at the next
+ * tick.  A generator's stream is sequential (Sec. 3.2), so its requests are
+ * served one after another in submission order; requests of different
+ * generators run in the same ticks.  Every result equals what the same
+ * generator's requests give alone, in order (tested).
+ */
+typedef struct mtgp_server mtgp_server;
+
+typedef struct mtgp_server_config {
+    uint64_t arena_bytes;      /* device memory for outputs, reserved at creation
+                                  (0 = 4 GiB)                                       */
+    uint64_t chunk;            /* numbers per request per tick (0 = 2^20)         */
+    uint32_t max_active;       /* requests generated concurrently (0 = 4096)       */
+    uint32_t max_inflight;     /* ticks queued on the GPU at once (0 = 2)          */
+} mtgp_server_config;
+
+typedef struct mtgp_completion {
+    uint64_t ticket;
+    uint32_t gen, dtype;
+    uint64_t n;
+    void *dev_out;             /* device address of the n outputs (in the arena),
+                                  valid until mtgp_server_release(ticket)          */
+    double submit_s, done_s;   /* seconds since the server was created: host clock
+                                  at submission, device event at completion        */
+} mtgp_completion;
+
+typedef struct mtgp_server_stats_t {
+    uint32_t pending, active, inflight_ticks;
+    uint64_t ticks, numbers_completed, arena_free_bytes;
+    double now_s;
+} mtgp_server_stats_t;
+
+/* Creates a server over pool p (which it uses exclusively, on `stream`);
+ * reserves the arena and captures the tick launch.  Synchronous. */
+mtgp_status mtgp_server_create(mtgp_pool *p, const mtgp_server_config *cfg, void *stream, mtgp_server **out);
+
+/* Queues a request; returns its ticket.  MTGP_EINVAL if n == 0, the generator
+ * or dtype is out of range, or 4 n bytes exceed the arena.  Host only. */
+mtgp_status mtgp_server_submit(mtgp_server *s, uint32_t gen, uint32_t dtype, uint64_t n, uint64_t *ticket);
+
+/* Advances the server (retire, admit, launch one tick if fewer than
+ * max_inflight are queued) and returns up to `max` completions in *done.  With
+ * block != 0 and nothing else to do, waits for the oldest queued tick. */
+mtgp_status mtgp_server_poll(mtgp_server *s, mtgp_completion *done, uint32_t max, uint32_t *ndone, int block);
+
+/* Returns a completed request's arena range to the server. */
+mtgp_status mtgp_server_release(mtgp_server *s, uint64_t ticket);
+
+mtgp_status mtgp_server_stats(const mtgp_server *s, mtgp_server_stats_t *out);
+
+/* Waits for queued ticks, then frees the arena, the graph and the server. */
+void mtgp_server_destroy(mtgp_server *s);
+
 /* ---- allocation-free form ---------------------------------------------------
  *
  * The paper has no counterpart to this call.  It exists for callers that must

@@ -54,6 +54,23 @@ class mtgp_config(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class mtgp_server_config(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_uint64), ("chunk", ctypes.c_uint64),
+                ("max_active", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32)]
+
+
+class mtgp_completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("gen", ctypes.c_uint32), ("dtype", ctypes.c_uint32),
+                ("n", ctypes.c_uint64), ("dev_out", ctypes.c_void_p), ("submit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
+class mtgp_server_stats_t(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_uint32), ("active", ctypes.c_uint32), ("inflight_ticks", ctypes.c_uint32),
+                ("ticks", ctypes.c_uint64), ("numbers_completed", ctypes.c_uint64),
+                ("arena_free_bytes", ctypes.c_uint64), ("now_s", ctypes.c_double)]
+
+
 _vp, _u32, _u64, _sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
 _P = ctypes.POINTER
 _SIGS = {
@@ -81,6 +98,18 @@ _SIGS = {
     "mtgp_autotune": (ctypes.c_int, [_vp, _P(mtgp_request), _u32, _vp, _vp, _P(mtgp_config),
                                      _P(ctypes.c_float)]),
     "mtgp_fill_probe": (ctypes.c_int, [_vp, _u64, _u32, _vp]),
+    "mtgp_pool_errors": (ctypes.c_int, [_vp, _P(_u32)]),
+    "mtgp_graph_create": (ctypes.c_int, [_vp, _u32, _vp, _P(_vp)]),
+    "mtgp_graph_set_requests": (ctypes.c_int, [_vp, _P(mtgp_request), _u32, _vp, ctypes.c_int, _vp]),
+    "mtgp_graph_launch": (ctypes.c_int, [_vp, _vp]),
+    "mtgp_graph_errors": (ctypes.c_int, [_vp, _P(_u32)]),
+    "mtgp_graph_destroy": (None, [_vp]),
+    "mtgp_server_create": (ctypes.c_int, [_vp, _P(mtgp_server_config), _vp, _P(_vp)]),
+    "mtgp_server_submit": (ctypes.c_int, [_vp, _u32, _u32, _u64, _P(_u64)]),
+    "mtgp_server_poll": (ctypes.c_int, [_vp, _P(mtgp_completion), _u32, _P(_u32), ctypes.c_int]),
+    "mtgp_server_release": (ctypes.c_int, [_vp, _u64]),
+    "mtgp_server_stats": (ctypes.c_int, [_vp, _P(mtgp_server_stats_t)]),
+    "mtgp_server_destroy": (None, [_vp]),
     "mtgp_generate_noalloc": (ctypes.c_int, [_P(mtgp_params), _u32, _vp, _P(_u64), _P(mtgp_request), _u32,
                                              _vp, _vp]),
 }

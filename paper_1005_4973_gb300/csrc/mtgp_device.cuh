@@ -520,13 +520,15 @@ __global__ void __launch_bounds__(2 * RT, (2 * RT) >= 512 ? 1 : 512 / (2 * RT)) 
     const uint32_t tid = threadIdx.x, lane = tid & 31u;
     const uint32_t B = a.buf_words;
     uint32_t item = blockIdx.x;
+    const uint32_t nwork = a.nwork_dev ? *a.nwork_dev : a.nwork;
+    uint32_t *const out = a.out_dev ? *a.out_dev : a.out;
     for (;;) {
         if (a.persistent) {
             if (tid == 0) s_item = atomicAdd(a.counter, 1u);
             __syncthreads();
             item = s_item;
         }
-        if (item >= a.nwork) break;
+        if (item >= nwork) break;
         const DevWork w = a.work[item];
         DevGen &gd = a.gens[w.gen];
         GenCtx g;
@@ -544,7 +546,7 @@ __global__ void __launch_bounds__(2 * RT, (2 * RT) >= 512 ? 1 : 512 / (2 * RT)) 
             uint32_t *st = a.state + gd.state_off;
             for (uint32_t j = tid; j < g.N; j += T) buf[j] = st[j];
             __syncthreads();
-            ok = dispatch_split<RT, QMAX>(nq, g, buf, B, w, a.segs + w.seg_begin, a.out, st);
+            ok = dispatch_split<RT, QMAX>(nq, g, buf, B, w, a.segs + w.seg_begin, out, st);
             if (ok && tid == 0) gd.count += w.total;
         }
         if (!ok && tid == 0) atomicOr(a.err, kErrBuffer);
@@ -561,13 +563,15 @@ __global__ void __launch_bounds__(T, QMAX <= 6 ? 512 / T : (T >= 256 ? 1 : 256 /
     const uint32_t tid = threadIdx.x, lane = tid & 31u;
     const uint32_t B = a.buf_words;
     uint32_t item = blockIdx.x;
+    const uint32_t nwork = a.nwork_dev ? *a.nwork_dev : a.nwork;
+    uint32_t *const out = a.out_dev ? *a.out_dev : a.out;
     for (;;) {
         if (a.persistent) {
             if (tid == 0) s_item = atomicAdd(a.counter, 1u);
             __syncthreads();
             item = s_item;
         }
-        if (item >= a.nwork) break;
+        if (item >= nwork) break;
         const DevWork w = a.work[item];
         DevGen &gd = a.gens[w.gen];
         GenCtx g;
@@ -585,7 +589,7 @@ __global__ void __launch_bounds__(T, QMAX <= 6 ? 512 / T : (T >= 256 ? 1 : 256 /
             uint32_t *st = a.state + gd.state_off;
             for (uint32_t j = tid; j < g.N; j += T) buf[j] = st[j];
             __syncthreads();
-            ok = dispatch_slots<T, QMAX>(nq, g, buf, B, w, a.segs + w.seg_begin, a.out, st);
+            ok = dispatch_slots<T, QMAX>(nq, g, buf, B, w, a.segs + w.seg_begin, out, st);
             if (ok && tid == 0) gd.count += w.total;
         }
         if (!ok && tid == 0) atomicOr(a.err, kErrBuffer);
@@ -887,13 +891,15 @@ __global__ void __launch_bounds__(64 * W, (64 * W) >= 512 ? 1 : 512 / (64 * W)) 
     const uint32_t tid = threadIdx.x, lane = tid & 31u;
     const uint32_t B = a.buf_words;
     uint32_t item = blockIdx.x;
+    const uint32_t nwork = a.nwork_dev ? *a.nwork_dev : a.nwork;
+    uint32_t *const out = a.out_dev ? *a.out_dev : a.out;
     for (;;) {
         if (a.persistent) {
             if (tid == 0) s_item = atomicAdd(a.counter, 1u);
             __syncthreads();
             item = s_item;
         }
-        if (item >= a.nwork) break;
+        if (item >= nwork) break;
         const DevWork w = a.work[item];
         DevGen &gd = a.gens[w.gen];
         GenCtx g;
@@ -913,7 +919,7 @@ __global__ void __launch_bounds__(64 * W, (64 * W) >= 512 ? 1 : 512 / (64 * W)) 
             for (uint32_t j = tid; j < g.N; j += T) buf[j] = st[j];
             if (tid < (uint32_t)W) prog[tid] = 0u;
             __syncthreads();
-            ok = dispatch_flow<W, CMAX>(nc, g, buf, B, w, a.segs + w.seg_begin, a.out, st, prog, a.err);
+            ok = dispatch_flow<W, CMAX>(nc, g, buf, B, w, a.segs + w.seg_begin, out, st, prog, a.err);
             if (ok && tid == 0) gd.count += w.total;
         }
         if (!ok && tid == 0) atomicOr(a.err, kErrBuffer);

@@ -175,6 +175,24 @@ struct mtgp_state {
     mtgp_pool *pool = nullptr;
 };
 
+// A captured persistent launch (see mtgp_graph_create).  Device buffer layout:
+// [0] work counter, [4] error word, [8] work-item count, [16] output base
+// pointer, [256 ..) DevWork[max_items], then DevSeg[max_items].
+struct mtgp_graph {
+    mtgp_pool *pool = nullptr;
+    uint32_t max_items = 0;
+    void *d_buf = nullptr;
+    size_t d_bytes = 0;
+    void *h_stage[2] = {nullptr, nullptr};   // pinned, alternating per upload
+    cudaEvent_t ev_stage[2] = {nullptr, nullptr};
+    bool stage_used[2] = {false, false};
+    int slot = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t B = 0;
+};
+
 namespace {
 
 const mtgp_config kDefaultConfig = {128u, 0u, 0u, 256u, 0u, 0u};
@@ -307,13 +325,15 @@ mtgp_status build_plan(const mtgp_pool *p, const mtgp_request *reqs, uint32_t nr
     return MTGP_OK;
 }
 
-mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStream_t s)
+// Kernel shape for a launch running the generators gens[0 .. n): slot count
+// qmax and shared buffer words B under configuration c (items = work items
+// expected, which sets how many blocks per SM the buffer is sized for).
+mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_t *gens, size_t n, size_t items,
+                         uint32_t *qmax_out, uint32_t *B_out)
 {
-    if (plan.work.empty()) return MTGP_OK;
-    const mtgp_config &c = p->cfg;
     uint32_t nmax = 0, smax = 0;
-    for (const DevWork &w : plan.work) {
-        const DevGen &g = p->host_gens[w.gen];
+    for (size_t i = 0; i < n; ++i) {
+        const DevGen &g = p->host_gens[gens[i]];
         nmax = std::max(nmax, g.N);
         smax = std::max(smax, g.N - g.M);
     }
@@ -322,12 +342,11 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     if (!qmax)
         return fail(MTGP_EINVAL, "no compiled kernel runs rounds of %u words with %u threads (form %u)", smax,
                     c.threads, c.form);
-    // shared buffer: at least 2N + T ceil(S/T) + 32 words (reads of the last
-    // column slot stay inside, compaction never overlaps); up to 32 rounds
-    // between compactions if the blocks wanted per SM fit
+    // shared buffer: at least the form's minimum; up to 32 rounds between
+    // compactions if the blocks wanted per SM fit
     uint32_t need = 0;
-    for (const DevWork &w : plan.work) {
-        const DevGen &g = p->host_gens[w.gen];
+    for (size_t i = 0; i < n; ++i) {
+        const DevGen &g = p->host_gens[gens[i]];
         const uint32_t S = g.N - g.M, nq = (S + owners - 1u) / owners;
         if (c.form == 2u)   // flow: epochs of at least N + S words between compactions
             need = std::max(need, 2u * g.N + 2u * S + 32u * nq + 32u);
@@ -337,16 +356,29 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     uint32_t B = c.buffer_words;
     if (!B) {
         uint32_t per_sm = c.persistent ? (c.blocks_per_sm ? c.blocks_per_sm : 2u)
-                                       : (uint32_t)std::min<size_t>(8, (plan.work.size() + p->sm_count - 1) /
-                                                                           (size_t)p->sm_count);
+                                       : (uint32_t)std::min<size_t>(8, (items + p->sm_count - 1) / (size_t)p->sm_count);
         per_sm = std::max(per_sm, 1u);
         const uint32_t budget = std::min(57344u, (uint32_t)((227u * 1024u / per_sm - 1024u) / 4u));
         B = std::min(2u * nmax + 32u * smax + 32u, budget);
         B = std::max(B, std::min(need + smax, 57344u));
         B = std::max(B, need);
     }
-    if (B < need) return fail(MTGP_EINVAL, "buffer_words %u < 2N + T ceil(S/T) + 32 = %u", B, need);
+    if (B < need) return fail(MTGP_EINVAL, "buffer_words %u below the minimum %u for this launch", B, need);
     if (B > 57344u) return fail(MTGP_EINVAL, "state too large for shared memory (%u words)", B);
+    *qmax_out = qmax;
+    *B_out = B;
+    return MTGP_OK;
+}
+
+mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStream_t s)
+{
+    if (plan.work.empty()) return MTGP_OK;
+    const mtgp_config &c = p->cfg;
+    std::vector<uint32_t> gens(plan.work.size());
+    for (size_t i = 0; i < plan.work.size(); ++i) gens[i] = plan.work[i].gen;
+    uint32_t qmax = 0, B = 0;
+    mtgp_status st0 = launch_shape(p, c, gens.data(), gens.size(), plan.work.size(), &qmax, &B);
+    if (st0 != MTGP_OK) return st0;
     // upload
     const size_t wbytes = plan.work.size() * sizeof(DevWork);
     const size_t sbytes = plan.segs.size() * sizeof(DevSeg);
@@ -858,6 +890,168 @@ mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
     if (st != MTGP_OK) return st;
     if (best) *best = best_c;
     if (best_ms) *best_ms = best_t;
+    return MTGP_OK;
+}
+
+// ---- graph-captured batched launch -------------------------------------------
+mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mtgp_graph **out)
+{
+    if (!p || !out || max_items == 0) return fail(MTGP_EINVAL, "graph: NULL pool/out or max_items == 0");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    mtgp_status st = pool_sync(p);
+    if (st != MTGP_OK) return st;
+    mtgp_config c = p->cfg;
+    c.persistent = 1u;                                   // a fixed grid pulls however many items there are
+    std::vector<uint32_t> all(p->count);
+    for (uint32_t i = 0; i < p->count; ++i) all[i] = i;  // any generator of the pool may appear
+    uint32_t qmax = 0, B = 0;
+    st = launch_shape(p, c, all.data(), all.size(), max_items, &qmax, &B);
+    if (st != MTGP_OK) return st;
+    int occ = 0;
+    CU(generate_occupancy(c.threads, c.form, qmax, B, &occ), "occupancy");
+    if (occ < 1) return fail(MTGP_EINVAL, "graph: configuration does not fit on an SM");
+    const int per_sm = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, occ) : occ;
+    const uint32_t grid = std::min<uint32_t>(max_items, (uint32_t)(per_sm * p->sm_count));
+    mtgp_graph *g = new (std::nothrow) mtgp_graph;
+    if (!g) return fail(MTGP_ENOMEM, "host allocation");
+    g->pool = p;
+    g->max_items = max_items;
+    g->B = B;
+    g->d_bytes = 256u + (size_t)max_items * (sizeof(DevWork) + sizeof(DevSeg));
+    auto bail = [&](mtgp_status r) { mtgp_graph_destroy(g); return r; };
+    cudaError_t e;
+#define CUG(call, what)                                       \
+    do {                                                      \
+        e = (call);                                           \
+        if (e != cudaSuccess) return bail(cuda_fail(e, what)); \
+    } while (0)
+    CUG(cudaMalloc(&g->d_buf, g->d_bytes), "cudaMalloc graph work list");
+    CUG(cudaMemsetAsync(g->d_buf, 0, 256u, s), "cudaMemsetAsync");
+    for (int k = 0; k < 2; ++k) {
+        CUG(cudaHostAlloc(&g->h_stage[k], g->d_bytes, cudaHostAllocDefault), "cudaHostAlloc");
+        CUG(cudaEventCreateWithFlags(&g->ev_stage[k], cudaEventDisableTiming), "cudaEventCreate");
+    }
+    CUG(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    CUG(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    char *b = (char *)g->d_buf;
+    LaunchArgs a{};
+    a.gens = p->d_gens;
+    a.state = p->d_state;
+    a.work = (const DevWork *)(b + 256u);
+    a.segs = (const DevSeg *)(b + 256u + (size_t)max_items * sizeof(DevWork));
+    a.out = nullptr;
+    a.counter = (unsigned *)b;
+    a.err = (unsigned *)(b + 4u);
+    a.nwork = 0;
+    a.nwork_dev = (const uint32_t *)(b + 8u);
+    a.out_dev = (uint32_t *const *)(b + 16u);
+    a.buf_words = B;
+    a.persistent = 1u;
+    CUG(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    cudaError_t e1 = cudaMemsetAsync(b, 0, sizeof(unsigned), g->cap_stream);
+    cudaError_t e2 = e1 == cudaSuccess ? launch_generate(a, c.threads, c.form, qmax, grid, g->cap_stream) : e1;
+    e = cudaStreamEndCapture(g->cap_stream, &g->graph);
+    if (e2 != cudaSuccess) return bail(cuda_fail(e2, "graph: capture of the generation launch"));
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamEndCapture"));
+    CUG(cudaGraphInstantiate(&g->exec, g->graph, 0), "cudaGraphInstantiate");
+#undef CUG
+    *out = g;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_graph_set_requests(mtgp_graph *g, const mtgp_request *reqs, uint32_t nreq, void *dev_out,
+                                    mtgp_layout layout, void *stream)
+{
+    if (!g) return fail(MTGP_EINVAL, "graph is NULL");
+    mtgp_pool *p = g->pool;
+    cudaStream_t s = (cudaStream_t)stream;
+    mtgp_status st = pool_busy_check(p, s);
+    if (st != MTGP_OK) return st;
+    const mtgp_config saved = p->cfg;
+    p->cfg.persistent = 1u;                              // longest-first order for the fixed grid
+    Plan plan;
+    st = build_plan(p, reqs, nreq, layout, &plan);
+    p->cfg = saved;
+    if (st != MTGP_OK) return st;
+    if (plan.work.size() > g->max_items || plan.segs.size() > g->max_items)
+        return fail(MTGP_EINVAL, "graph: %zu work items / %zu segments exceed its capacity %u", plan.work.size(),
+                    plan.segs.size(), g->max_items);
+    if (plan.total && !dev_out) return fail(MTGP_EINVAL, "dev_out is NULL");
+    if (((uintptr_t)dev_out & 3u) != 0) return fail(MTGP_EINVAL, "dev_out must be 4-byte aligned");
+    const int k = g->slot;
+    if (g->stage_used[k]) CU(cudaEventSynchronize(g->ev_stage[k]), "cudaEventSynchronize");
+    char *h = (char *)g->h_stage[k];
+    const uint32_t nwork = (uint32_t)plan.work.size();
+    std::memcpy(h + 8u, &nwork, sizeof nwork);
+    std::memcpy(h + 16u, &dev_out, sizeof dev_out);
+    std::memcpy(h + 256u, plan.work.data(), plan.work.size() * sizeof(DevWork));
+    const size_t seg_off = 256u + (size_t)g->max_items * sizeof(DevWork);
+    std::memcpy(h + seg_off, plan.segs.data(), plan.segs.size() * sizeof(DevSeg));
+    // control words from [8, 24), then the work items, then the segments
+    CU(cudaMemcpyAsync((char *)g->d_buf + 8u, h + 8u, 248u + plan.work.size() * sizeof(DevWork),
+                       cudaMemcpyHostToDevice, s),
+       "graph: upload work list");
+    if (!plan.segs.empty())
+        CU(cudaMemcpyAsync((char *)g->d_buf + seg_off, h + seg_off, plan.segs.size() * sizeof(DevSeg),
+                           cudaMemcpyHostToDevice, s),
+           "graph: upload segments");
+    CU(cudaEventRecord(g->ev_stage[k], s), "cudaEventRecord");
+    g->stage_used[k] = true;
+    g->slot ^= 1;
+    p->last_stream = s;
+    CU(cudaEventRecord(p->ev_done, s), "cudaEventRecord");
+    p->used = true;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_graph_launch(mtgp_graph *g, void *stream)
+{
+    if (!g) return fail(MTGP_EINVAL, "graph is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    mtgp_status st = pool_busy_check(g->pool, s);
+    if (st != MTGP_OK) return st;
+    CU(cudaGraphLaunch(g->exec, s), "cudaGraphLaunch");
+    CU(cudaEventRecord(g->pool->ev_done, s), "cudaEventRecord");
+    g->pool->last_stream = s;
+    g->pool->used = true;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_graph_errors(mtgp_graph *g, uint32_t *flags)
+{
+    if (!g || !flags) return fail(MTGP_EINVAL, "NULL argument");
+    mtgp_status st = pool_sync(g->pool);
+    if (st != MTGP_OK) return st;
+    CU(cudaMemcpy(flags, (char *)g->d_buf + 4u, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read error word");
+    CU(cudaMemset((char *)g->d_buf + 4u, 0, sizeof(uint32_t)), "clear error word");
+    return MTGP_OK;
+}
+
+void mtgp_graph_destroy(mtgp_graph *g)
+{
+    if (!g) return;
+    if (g->pool && g->pool->used) cudaEventSynchronize(g->pool->ev_done);
+    for (int k = 0; k < 2; ++k) {
+        if (g->stage_used[k]) cudaEventSynchronize(g->ev_stage[k]);
+        if (g->ev_stage[k]) cudaEventDestroy(g->ev_stage[k]);
+        if (g->h_stage[k]) cudaFreeHost(g->h_stage[k]);
+    }
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    cudaFree(g->d_buf);
+    delete g;
+}
+
+// ---- error words -----------------------------------------------------------------
+mtgp_status mtgp_pool_errors(mtgp_pool *p, uint32_t *flags)
+{
+    if (!p || !flags) return fail(MTGP_EINVAL, "NULL argument");
+    mtgp_status st = pool_sync(p);
+    if (st != MTGP_OK) return st;
+    CU(cudaMemcpy(flags, p->d_ctl + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read error word");
+    CU(cudaMemset(p->d_ctl + 1, 0, sizeof(uint32_t)), "clear error word");
     return MTGP_OK;
 }
 

@@ -51,7 +51,12 @@ struct LaunchArgs {
     unsigned *counter;            // persistent work counter, zero at launch
     unsigned *err;
     uint32_t nwork;
-    uint32_t buf_words;           // shared buffer, >= 2N + S + 32 words for every item
+    uint32_t buf_words;
+    // Graph form: when set, the work-item count and the output base are read
+    // from these device words at launch, so one captured launch can be
+    // replayed with a new work list.
+    const uint32_t *nwork_dev;
+    uint32_t *const *out_dev;           // shared buffer, >= 2N + S + 32 words for every item
     uint32_t persistent;
 };
 

@@ -113,8 +113,13 @@ cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t form
     GenKernel k = pick(threads, form, qmax);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = (size_t)a.buf_words * sizeof(uint32_t);
-    if (smem + 1024u > 48u * 1024u) {     // dynamic + the kernels' static words past the default
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
+    // dynamic + the kernels' static words past the default limit (set before
+    // a capture by generate_occupancy; a function attribute is not captured)
+    if (smem + 1024u > 48u * 1024u && cap == cudaStreamCaptureStatusNone) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     k<<<grid, threads, smem, s>>>(a);

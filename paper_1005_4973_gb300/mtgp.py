@@ -1,5 +1,5 @@
-"""Python face of libmtgp.  Same names as the C ABI (include/mtgp.h), plus two
-small owner classes (Pool, State) that free their handles.  Marshalling only:
+"""Python face of libmtgp.  Same names as the C ABI (include/mtgp.h), plus small
+owner classes (Pool, State, Graph, Server) that free their handles.  Marshalling only:
 every number is produced by the CUDA kernels behind the C ABI.
 """
 from __future__ import annotations
@@ -99,6 +99,12 @@ class Pool:
     def load(self, blob: bytes) -> None:
         L.check(L.LIB.mtgp_pool_load(self.handle, blob, len(blob)))
 
+    def errors(self) -> int:
+        """Error word of the last launches (bit 0 shape/buffer, bit 1 wait timeout); clears it."""
+        v = ctypes.c_uint32()
+        L.check(L.LIB.mtgp_pool_errors(self.handle, ctypes.byref(v)))
+        return v.value
+
     def info(self):
         c, b = ctypes.c_uint32(), ctypes.c_uint64()
         L.check(L.LIB.mtgp_pool_info(self.handle, ctypes.byref(c), ctypes.byref(b)))
@@ -147,6 +153,80 @@ class State:
     def close(self) -> None:
         if self.handle:
             L.LIB.mtgp_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """Captured persistent launch over a pool (mtgp_graph_*)."""
+
+    def __init__(self, pool: Pool, max_items: int, stream=None):
+        h = ctypes.c_void_p()
+        L.check(L.LIB.mtgp_graph_create(pool.handle, max_items, L.stream_handle(stream), ctypes.byref(h)))
+        self.handle, self.pool = h, pool
+
+    def set_requests(self, reqs, out, layout=MTGP_LAYOUT_BLOCKED, stream=None) -> None:
+        arr = L.requests_array(reqs)
+        L.check(L.LIB.mtgp_graph_set_requests(self.handle, arr, len(reqs), L.ptr(out), layout,
+                                              L.stream_handle(stream)))
+
+    def launch(self, stream=None) -> None:
+        L.check(L.LIB.mtgp_graph_launch(self.handle, L.stream_handle(stream)))
+
+    def errors(self) -> int:
+        v = ctypes.c_uint32()
+        L.check(L.LIB.mtgp_graph_errors(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def close(self) -> None:
+        if self.handle:
+            L.LIB.mtgp_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server over a pool (mtgp_server_*)."""
+
+    def __init__(self, pool: Pool, arena_bytes=0, chunk=0, max_active=0, max_inflight=0, stream=None):
+        cfg = L.mtgp_server_config(arena_bytes, chunk, max_active, max_inflight)
+        h = ctypes.c_void_p()
+        L.check(L.LIB.mtgp_server_create(pool.handle, ctypes.byref(cfg), L.stream_handle(stream),
+                                         ctypes.byref(h)))
+        self.handle, self.pool = h, pool
+        self._buf = (L.mtgp_completion * 256)()
+
+    def submit(self, gen: int, dtype: int, n: int) -> int:
+        t = ctypes.c_uint64()
+        L.check(L.LIB.mtgp_server_submit(self.handle, gen, dtype, n, ctypes.byref(t)))
+        return t.value
+
+    def poll(self, block: bool = False):
+        nd = ctypes.c_uint32()
+        L.check(L.LIB.mtgp_server_poll(self.handle, self._buf, len(self._buf), ctypes.byref(nd), int(block)))
+        return [self._buf[i] for i in range(nd.value)]
+
+    def release(self, ticket: int) -> None:
+        L.check(L.LIB.mtgp_server_release(self.handle, ticket))
+
+    def stats(self):
+        st = L.mtgp_server_stats_t()
+        L.check(L.LIB.mtgp_server_stats(self.handle, ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in st._fields_}
+
+    def close(self) -> None:
+        if self.handle:
+            L.LIB.mtgp_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MTGP Gnum/s & HBM write GB/s vs peak (plain vs batched); served p50/p99 latency"
 KERNEL_SOURCES = ["paper_1005_4973_gb300/csrc/mtgp_device.cuh", "paper_1005_4973_gb300/csrc/mtgp_internal.h"]
-NCU_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+NCU_SUMMARY = os.path.join(ROOT, "profiles", "k_generate_c2_plain.md")
 
 
 def kernel_hash() -> str:
@@ -122,7 +122,7 @@ class ClockSampler:
                 "samples": len(rows), "window": window}
 
 
-def cpu_baseline(wl, numbers_per_gen: int, batch: int = 64):
+def cpu_baseline(wl, numbers_per_gen: int, batch: int = 32):
     """The oracle, as it stands, on the host cores over a bounded sample."""
     import oracle as O
     O.build()
@@ -182,6 +182,94 @@ def run_reference(args, rank, world):
     }))
 
 
+def run_batched(torch, M, sample: int = 512):
+    """C4: 8192 generators in one graph-captured persistent launch (timed over
+    replays), against one plain single-generator launch per generator on the
+    first `sample` generators (same streams, timed separately)."""
+    from paper_1005_4973_gb300 import workloads as WL
+    wl = WL.c4()
+    ps = [M.mtgp_params_draw(g.mexp, g.param_seed, g.id) for g in wl.gens]
+    pool = M.Pool(ps, [g.gen_id for g in wl.gens], [g.seed for g in wl.gens])
+    pool.set_config(threads=256, persistent=1)
+    total = wl.total_numbers
+    out = torch.empty(total, dtype=torch.int32, device="cuda")
+    graph = M.Graph(pool, max_items=len(wl.gens))
+    graph.set_requests(wl.requests, out)
+    for _ in range(2):
+        graph.launch()
+    steps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        graph.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    assert graph.errors() == 0
+    graph.close()
+    # one plain launch per generator (a one-request call each), first `sample` generators
+    sub = wl.requests[:sample]
+    n_sub = sum(r[2] for r in sub)
+    for r in sub[:8]:
+        pool.generate([r], out)
+    torch.cuda.synchronize()
+    e0.record()
+    for r in sub:
+        pool.generate([r], out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    pool.close()
+    return {"workload": "C4: 8192 generators, mexp uniform over {11213, 23209, 44497}, lengths "
+                        "floor(2^U(10,24)), u32/f[0,1) alternating, blocked",
+            "value": total / (ms * 1e-3) / 1e9, "unit": "Gnum/s", "ms_per_launch": ms,
+            "hbm_write_gbs": 4 * total / (ms * 1e-3) / 1e9, "numbers": total,
+            "form": "one graph-captured persistent launch (256 threads, longest first)",
+            "plain_per_generator": {"value": n_sub / (ms_plain * 1e-3) / 1e9, "unit": "Gnum/s",
+                                    "generators": len(sub), "launches": len(sub),
+                                    "note": "one launch per generator, first %d generators of C4" % len(sub)}}
+
+
+def run_served(torch, M, batched_gnums: float, fracs=(0.25, 0.5, 0.8), requests: int = 10000,
+               warm: int = 1000):
+    """C5: Poisson arrivals over 65536 resident generators at fractions of the
+    measured batched rate, run by the library's native request loop; p50/p99
+    latency (device completion minus host submission) over `requests` requests
+    after `warm` warm-up arrivals."""
+    import numpy as np
+    from paper_1005_4973_gb300 import workloads as WL
+    gens = WL.c5_pool()
+    ps = [M.mtgp_params_draw(g.mexp, g.param_seed, g.id) for g in gens]
+    pool = M.Pool(ps, [g.gen_id for g in gens], [g.seed for g in gens])
+    pool.set_config(threads=256)
+    mean_len = WL.expected_log_uniform_len(8.0, 26.0)
+    results = []
+    for frac in fracs:
+        rate = frac * batched_gnums * 1e9 / mean_len
+        arrivals = WL.c5_arrivals(rate, warm + requests, pool_size=len(gens), seed=13 + int(100 * frac))
+        srv = M.Server(pool, arena_bytes=24 << 30, chunk=1 << 22, max_active=4096)
+        lat, done = srv.run_trace(arrivals)
+        st = srv.stats()
+        srv.close()
+        arr = np.array([a[0] for a in arrivals[warm:]])
+        n = np.array([a[3] for a in arrivals[warm:]], dtype=np.float64)
+        lat_ms = lat[warm:] * 1e3
+        span = float(done[warm:].max() - arr.min())
+        results.append({"rate_frac": frac, "rate_req_s": rate, "requests": requests, "warmup_requests": warm,
+                        "offered_gnums": float(n.sum() / (arr.max() - arr.min()) / 1e9),
+                        "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                        "mean_ms": float(lat_ms.mean()),
+                        "sustained_gnums": float(n.sum() / span / 1e9) if span > 0 else None,
+                        "ticks": int(st["ticks"])})
+    pool.close()
+    return {"workload": "C5: 65536 resident generators (mexp mix as C4), Poisson arrivals, lengths "
+                        "floor(2^U(8,26)), u32/f[0,1) 50/50, continuous batching",
+            "mean_len": mean_len, "chunk": 1 << 22, "max_active": 4096,
+            "latency": "device completion event minus host submission", "loop": "mtgp_server_run_trace (native)",
+            "rates": results}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,9 +280,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-numbers", type=int, default=1 << 22, help="numbers per generator in the CPU sample")
-    ap.add_argument("--ref-numbers", type=int, default=1 << 16, help="numbers per generator per reference step")
-    ap.add_argument("--config", default="", help="JSON launch config overrides (threads, slots, persistent, ...)")
+    ap.add_argument("--cpu-numbers", type=int, default=1 << 24, help="numbers per generator in the CPU sample")
+    ap.add_argument("--ref-numbers", type=int, default=1 << 20, help="numbers per generator per reference step")
+    ap.add_argument("--config", default="", help="JSON launch config overrides (threads, form, persistent, ...)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched (C4) and served (C5) measurements")
+    ap.add_argument("--serve-requests", type=int, default=10000, help="C5 requests timed per arrival rate")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -280,12 +370,16 @@ def main():
     alg_bytes = 4 * total + state_bytes                  # per launch: outputs + state load/store
     avg_launch = statistics.mean(launch_ms)
     achieved = alg_bytes / (avg_launch * 1e-3) / 1e9
-    traffic = None
-    if os.path.exists(NCU_TRAFFIC):
-        with open(NCU_TRAFFIC) as f:
-            tr = json.load(f)
-        if tr.get("kernel_hash") == kernel_hash() and tr.get("workload") == args.workload:
-            traffic = tr.get("bytes_per_launch")
+    traffic = None                                       # ncu DRAM bytes, scaled to this launch
+    if os.path.exists(NCU_SUMMARY) and args.workload in ("c2", "c2s"):
+        fields = {}
+        with open(NCU_SUMMARY) as f:
+            for ln in f:
+                if ":" in ln and ln.split(":", 1)[0].strip() in ("kernel_hash", "traffic_bytes_per_number"):
+                    k, v = ln.split(":", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+        if fields.get("kernel_hash") == kernel_hash() and "traffic_bytes_per_number" in fields:
+            traffic = float(fields["traffic_bytes_per_number"]) * total
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -307,6 +401,14 @@ def main():
         cpu = {"value": v, "unit": "Gnum/s", "cores": cores, "kind": "oracle",
                "sample": f"all {len(wl.gens)} generator instances of {wl.name} x {args.cpu_numbers} numbers "
                          f"({done:.3g} numbers, {dt:.1f} s)"}
+
+    extras = {}
+    if not args.no_extras and rank == 0 and world == 1 and args.workload == "c2":
+        del out
+        torch.cuda.empty_cache()
+        extras["batched"] = run_batched(torch, M)
+        torch.cuda.empty_cache()
+        extras["served"] = run_served(torch, M, extras["batched"]["value"], requests=args.serve_requests)
 
     if rank == 0:
         line = {
@@ -332,6 +434,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
             "kernel_hash": kernel_hash(),
         }
+        line.update(extras)
         print(json.dumps(line))
     if sampler:
         sampler.stop()

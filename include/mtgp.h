@@ -359,6 +359,19 @@ mtgp_status mtgp_server_release(mtgp_server *s, uint64_t ticket);
 
 mtgp_status mtgp_server_stats(const mtgp_server *s, mtgp_server_stats_t *out);
 
+/*
+ * Native request loop over an arrival trace: submits request i (generator
+ * gens[i], dtype dtypes[i], ns[i] numbers) when arrival_s[i] seconds
+ * (non-decreasing, from the call) have passed on the host clock, polls, and
+ * releases each completed output at once.  Writes each request's latency
+ * (device completion minus host submission) to latency_s[i] and, if done_s is
+ * not NULL, its completion time since the call.  Returns when all complete.
+ * For measuring the served form without a host-language loop in the way.
+ */
+mtgp_status mtgp_server_run_trace(mtgp_server *s, const double *arrival_s, const uint32_t *gens,
+                                  const uint32_t *dtypes, const uint64_t *ns, uint32_t count, double *latency_s,
+                                  double *done_s);
+
 /* Waits for queued ticks, then frees the arena, the graph and the server. */
 void mtgp_server_destroy(mtgp_server *s);
 

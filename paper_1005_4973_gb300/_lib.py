@@ -110,6 +110,8 @@ _SIGS = {
     "mtgp_server_release": (ctypes.c_int, [_vp, _u64]),
     "mtgp_server_stats": (ctypes.c_int, [_vp, _P(mtgp_server_stats_t)]),
     "mtgp_server_destroy": (None, [_vp]),
+    "mtgp_server_run_trace": (ctypes.c_int, [_vp, _P(ctypes.c_double), _P(_u32), _P(_u32), _P(_u64), _u32,
+                                             _P(ctypes.c_double), _P(ctypes.c_double)]),
     "mtgp_generate_noalloc": (ctypes.c_int, [_P(mtgp_params), _u32, _vp, _P(_u64), _P(mtgp_request), _u32,
                                              _vp, _vp]),
 }

@@ -62,6 +62,8 @@ struct mtgp_server {
     uint64_t next_ticket = 1;
     uint64_t numbers_done = 0, ticks = 0;
     std::vector<mtgp_request> tick_reqs;
+    std::vector<uint32_t> held_mark;               // == held_stamp: generator held back this pass
+    uint32_t held_stamp = 0;
 
     double now_s() const
     {
@@ -212,13 +214,17 @@ mtgp_status retire(mtgp_server *s, bool wait)
 // cannot be admitted holds back the later requests of its generator.
 void admit(mtgp_server *s)
 {
-    std::vector<uint8_t> held(0);
+    if (s->held_mark.size() != s->count) s->held_mark.assign(s->count, 0);
+    if (++s->held_stamp == 0) {                   // stamp wrapped: clear the marks once
+        std::fill(s->held_mark.begin(), s->held_mark.end(), 0u);
+        s->held_stamp = 1;
+    }
+    const uint32_t stamp = s->held_stamp;
     for (auto it = s->pending.begin(); it != s->pending.end();) {
         if (s->active.size() >= s->cfg.max_active) break;
         Req &r = s->reqs[*it];
-        if (held.empty()) held.assign(s->count, 0);
-        if (s->gen_busy[r.gen] || held[r.gen] || !s->alloc(r.bytes, &r.off)) {
-            held[r.gen] = 1;
+        if (s->gen_busy[r.gen] || s->held_mark[r.gen] == stamp || !s->alloc(r.bytes, &r.off)) {
+            s->held_mark[r.gen] = stamp;
             ++it;
             continue;
         }
@@ -339,3 +345,39 @@ void mtgp_server_destroy(mtgp_server *s)
 }
 
 }  // extern "C"
+
+extern "C" mtgp_status mtgp_server_run_trace(mtgp_server *s, const double *arrival_s, const uint32_t *gens,
+                                             const uint32_t *dtypes, const uint64_t *ns, uint32_t count,
+                                             double *latency_s, double *done_s)
+{
+    if (!s || (count && (!arrival_s || !gens || !dtypes || !ns || !latency_s))) return fail(MTGP_EINVAL, "trace: NULL argument");
+    std::unordered_map<uint64_t, uint32_t> index;     // ticket -> position in the trace
+    index.reserve(count * 2u + 1u);
+    std::vector<mtgp_completion> buf(1024);
+    const double start = s->now_s();
+    uint32_t next = 0, finished = 0;
+    for (uint32_t i = 0; i < count; ++i)
+        if (i && arrival_s[i] < arrival_s[i - 1]) return fail(MTGP_EINVAL, "trace: arrival times must not decrease");
+    while (finished < count) {
+        const double now = s->now_s() - start;
+        while (next < count && arrival_s[next] <= now) {
+            uint64_t t = 0;
+            mtgp_status st = mtgp_server_submit(s, gens[next], dtypes[next], ns[next], &t);
+            if (st != MTGP_OK) return st;
+            index[t] = next++;
+        }
+        uint32_t nd = 0;
+        mtgp_status st = mtgp_server_poll(s, buf.data(), (uint32_t)buf.size(), &nd, next == count ? 1 : 0);
+        if (st != MTGP_OK) return st;
+        for (uint32_t j = 0; j < nd; ++j) {
+            const uint32_t i = index[buf[j].ticket];
+            latency_s[i] = buf[j].done_s - buf[j].submit_s;
+            if (done_s) done_s[i] = buf[j].done_s - start;
+            index.erase(buf[j].ticket);
+            st = mtgp_server_release(s, buf[j].ticket);
+            if (st != MTGP_OK) return st;
+            ++finished;
+        }
+    }
+    return MTGP_OK;
+}

@@ -219,6 +219,23 @@ class Server:
     def release(self, ticket: int) -> None:
         L.check(L.LIB.mtgp_server_release(self.handle, ticket))
 
+    def run_trace(self, arrivals):
+        """arrivals: list of (time_s, gen, dtype, n), sorted by time.  Runs the
+        native request loop; returns (latency_s, done_s) numpy arrays."""
+        k = len(arrivals)
+        a = np.ascontiguousarray([x[0] for x in arrivals], dtype=np.float64)
+        g = np.ascontiguousarray([x[1] for x in arrivals], dtype=np.uint32)
+        d = np.ascontiguousarray([x[2] for x in arrivals], dtype=np.uint32)
+        n = np.ascontiguousarray([x[3] for x in arrivals], dtype=np.uint64)
+        lat = np.zeros(k, dtype=np.float64)
+        done = np.zeros(k, dtype=np.float64)
+        P = ctypes.POINTER
+        L.check(L.LIB.mtgp_server_run_trace(
+            self.handle, a.ctypes.data_as(P(ctypes.c_double)), g.ctypes.data_as(P(ctypes.c_uint32)),
+            d.ctypes.data_as(P(ctypes.c_uint32)), n.ctypes.data_as(P(ctypes.c_uint64)), k,
+            lat.ctypes.data_as(P(ctypes.c_double)), done.ctypes.data_as(P(ctypes.c_double))))
+        return lat, done
+
     def stats(self):
         st = L.mtgp_server_stats_t()
         L.check(L.LIB.mtgp_server_stats(self.handle, ctypes.byref(st)))

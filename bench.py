@@ -344,6 +344,7 @@ def main():
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    launches0 = pool.launch_count()
     t_host0 = time.perf_counter()
     e0.record(stream)
     for k in range(args.steps):
@@ -353,6 +354,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     t_host1 = time.perf_counter()
+    launches = pool.launch_count() - launches0
     if dist:
         dist.barrier()
     ms_total = e0.elapsed_time(e1)
@@ -431,7 +433,7 @@ def main():
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "k_generate", "alg_bytes_per_launch": alg_bytes,
                          "avg_launch_ms": avg_launch, "frac_of_write_probe": achieved / write_probe_gbs},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "kernel_hash": kernel_hash(),
         }
         line.update(extras)

@@ -112,6 +112,14 @@ typedef struct mtgp_config {
                                   handing rounds over through named barriers),
                                   2 flow (split groups, and each recursion warp
                                   waits only for the warps holding its inputs)       */
+    uint32_t pieces;           /* jump-ahead (Sec. 7): a generator's work in one call
+                                  (blocked layout) may run as up to this many pieces
+                                  on separate blocks, piece m starting from the state
+                                  m L numbers ahead, computed on the GPU before the
+                                  launch; outputs are identical.  0 = auto (about 16
+                                  blocks per SM), 1 = never split                    */
+    uint32_t piece_log2;       /* pieces hold at least 2^piece_log2 numbers; 0 = 20,
+                                  else 10 .. 40                                      */
 } mtgp_config;
 
 /* ---- library ------------------------------------------------------------ */
@@ -266,6 +274,57 @@ mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
  * that set a bit are invalid.
  */
 mtgp_status mtgp_pool_errors(mtgp_pool *p, uint32_t *flags);
+
+/* Kernels launched so far by the pool's generation calls (generation, plus
+ * the two jump-ahead kernels of calls that split work into pieces). */
+mtgp_status mtgp_pool_launch_count(const mtgp_pool *p, uint64_t *launches);
+
+/* ---- jump-ahead (Sec. 7) ------------------------------------------------------
+ *
+ * Sec. 7 observes that one generator's stream can be produced by several
+ * processors if the state n outputs ahead can be computed without producing
+ * them.  For a state s of the linear transition F (Sec. 3.3) the library finds
+ * an annihilating polynomial psi, psi(F) s = 0: the Berlekamp-Massey minimal
+ * polynomial of a bit sequence read off the walk from s (a linear functional
+ * of the state), checked on the GPU by computing phi(F) s and repeated on the
+ * remainder until it vanishes.  Then F^J s = g(F) s with g = x^J mod psi, an
+ * XOR of the states F^i s that g's coefficients select.  psi of a state also
+ * annihilates every later state, so it is computed once per generator (and
+ * again after mtgp_pool_load).  The pool uses this to split long requests
+ * into pieces (mtgp_config.pieces); the calls below expose it directly.
+ */
+
+/* Advances generator i by `steps` outputs without producing them: state and
+ * position become exactly those after generating `steps` numbers.  The first
+ * use for a generator computes psi (GPU walk plus host Berlekamp-Massey:
+ * milliseconds for mexp 11213, about a second for 44497); each jump then
+ * costs O(log steps) polynomial squarings modulo psi on the host and one
+ * O(mexp N) GPU pass.  Synchronous. */
+mtgp_status mtgp_pool_jump(mtgp_pool *p, uint32_t i, uint64_t steps, void *stream);
+mtgp_status mtgp_state_jump(mtgp_state *s, uint64_t steps, void *stream);
+
+/* psi of generator i's current stream (computed if not known yet): its degree
+ * (<= mexp) goes to *degree and its coefficients to poly (bit j of word j/64 =
+ * coefficient of x^j) if poly_words >= degree / 64 + 1; with poly NULL only
+ * the degree is returned.  MTGP_EINVAL if poly is too small.  Synchronous. */
+mtgp_status mtgp_pool_annihilator(mtgp_pool *p, uint32_t i, uint64_t *poly, uint32_t poly_words,
+                                  uint32_t *degree, void *stream);
+
+/* F2[x] routines behind jump-ahead (host only, pure).  A polynomial is a
+ * little-endian array of 64-bit words: bit j of word j/64 is the coefficient
+ * of x^j.  *deg receives the result's degree (-1 for zero).  MTGP_EINVAL if a
+ * pointer is NULL, the modulus has degree < 1, or out has fewer than
+ * deg / 64 + 1 words (then *deg still holds the degree).
+ *   minpoly:  minimal polynomial of the bit sequence bits[0 .. n) (bit i of
+ *             bits[i/64]) in annihilator form, sum_j c_j s_{k+j} = 0 for all k
+ *             (Berlekamp-Massey; exact when the linear complexity <= n/2)
+ *   mulmod:   a b mod m
+ *   xpow_mod: x^e mod m */
+mtgp_status mtgp_f2_minpoly(const uint64_t *bits, uint64_t n, uint64_t *out, uint32_t out_words, int64_t *deg);
+mtgp_status mtgp_f2_mulmod(const uint64_t *a, uint32_t a_words, const uint64_t *b, uint32_t b_words,
+                           const uint64_t *m, uint32_t m_words, uint64_t *out, uint32_t out_words, int64_t *deg);
+mtgp_status mtgp_f2_xpow_mod(uint64_t e, const uint64_t *m, uint32_t m_words, uint64_t *out, uint32_t out_words,
+                             int64_t *deg);
 
 /* ---- graph-captured batched launch --------------------------------------------
  *

@@ -48,7 +48,8 @@ class mtgp_request(ctypes.Structure):
 
 class mtgp_config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
-                ("threads", "persistent", "blocks_per_sm", "chunk", "buffer_words", "form")]
+                ("threads", "persistent", "blocks_per_sm", "chunk", "buffer_words", "form", "pieces",
+                 "piece_log2")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -99,6 +100,14 @@ _SIGS = {
                                      _P(ctypes.c_float)]),
     "mtgp_fill_probe": (ctypes.c_int, [_vp, _u64, _u32, _vp]),
     "mtgp_pool_errors": (ctypes.c_int, [_vp, _P(_u32)]),
+    "mtgp_pool_launch_count": (ctypes.c_int, [_vp, _P(_u64)]),
+    "mtgp_pool_jump": (ctypes.c_int, [_vp, _u32, _u64, _vp]),
+    "mtgp_state_jump": (ctypes.c_int, [_vp, _u64, _vp]),
+    "mtgp_pool_annihilator": (ctypes.c_int, [_vp, _u32, _P(_u64), _u32, _P(_u32), _vp]),
+    "mtgp_f2_minpoly": (ctypes.c_int, [_P(_u64), _u64, _P(_u64), _u32, _P(ctypes.c_int64)]),
+    "mtgp_f2_mulmod": (ctypes.c_int, [_P(_u64), _u32, _P(_u64), _u32, _P(_u64), _u32, _P(_u64), _u32,
+                                      _P(ctypes.c_int64)]),
+    "mtgp_f2_xpow_mod": (ctypes.c_int, [_u64, _P(_u64), _u32, _P(_u64), _u32, _P(ctypes.c_int64)]),
     "mtgp_graph_create": (ctypes.c_int, [_vp, _u32, _vp, _P(_vp)]),
     "mtgp_graph_set_requests": (ctypes.c_int, [_vp, _P(mtgp_request), _u32, _vp, ctypes.c_int, _vp]),
     "mtgp_graph_launch": (ctypes.c_int, [_vp, _vp]),

@@ -236,7 +236,8 @@ __device__ __forceinline__ void run_item(const GenCtx g, uint32_t *buf, uint32_t
             k0 += S_r;
         }
     }
-    for (uint32_t j = tid; j < g.N; j += T) st[j] = buf[rel + j];   // state write-back (Sec. 8)
+    if (st)                                              // state write-back (Sec. 8)
+        for (uint32_t j = tid; j < g.N; j += T) st[j] = buf[rel + j];
 }
 
 // Runs the work item with the slot count Q = ceil(S / T) it needs, searching
@@ -362,7 +363,8 @@ __device__ __forceinline__ void split_recursion(const GenCtx &g, uint32_t *buf, 
     }
     for (uint32_t j = (rounds > drained + kRing ? rounds - kRing : drained); j < rounds; ++j)
         nb_sync(bar_empty(j), ALL);
-    for (uint32_t j = rt; j < g.N; j += RT) st[j] = buf[rel + j];   // state write-back (Sec. 8)
+    if (st)                                              // state write-back (Sec. 8)
+        for (uint32_t j = rt; j < g.N; j += RT) st[j] = buf[rel + j];
 }
 
 // Output group: one round's Q slots inside one blocked segment of dtype DT.
@@ -544,10 +546,13 @@ __global__ void __launch_bounds__(2 * RT, (2 * RT) >= 512 ? 1 : 512 / (2 * RT)) 
         bool ok = nq <= (uint32_t)QMAX && 2u * g.N + nq * RT + 32u <= B;
         if (ok) {
             uint32_t *st = a.state + gd.state_off;
-            for (uint32_t j = tid; j < g.N; j += T) buf[j] = st[j];
+            const bool piece = (w.flags & kItemPiece) != 0u;   // jump-ahead piece (Sec. 7)
+            const uint32_t *ld = piece ? a.jstate + w.src : st;
+            if (piece && !(w.flags & kItemLast)) st = nullptr;
+            for (uint32_t j = tid; j < g.N; j += T) buf[j] = ld[j];
             __syncthreads();
             ok = dispatch_split<RT, QMAX>(nq, g, buf, B, w, a.segs + w.seg_begin, out, st);
-            if (ok && tid == 0) gd.count += w.total;
+            if (ok && tid == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&gd.count), (unsigned long long)w.total);
         }
         if (!ok && tid == 0) atomicOr(a.err, kErrBuffer);
         __syncthreads();                                     // buffer and s_item reuse
@@ -587,10 +592,13 @@ __global__ void __launch_bounds__(T, QMAX <= 6 ? 512 / T : (T >= 256 ? 1 : 256 /
         bool ok = nq <= (uint32_t)QMAX && 2u * g.N + nq * T + 32u <= B;
         if (ok) {
             uint32_t *st = a.state + gd.state_off;
-            for (uint32_t j = tid; j < g.N; j += T) buf[j] = st[j];
+            const bool piece = (w.flags & kItemPiece) != 0u;   // jump-ahead piece (Sec. 7)
+            const uint32_t *ld = piece ? a.jstate + w.src : st;
+            if (piece && !(w.flags & kItemLast)) st = nullptr;
+            for (uint32_t j = tid; j < g.N; j += T) buf[j] = ld[j];
             __syncthreads();
             ok = dispatch_slots<T, QMAX>(nq, g, buf, B, w, a.segs + w.seg_begin, out, st);
-            if (ok && tid == 0) gd.count += w.total;
+            if (ok && tid == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&gd.count), (unsigned long long)w.total);
         }
         if (!ok && tid == 0) atomicOr(a.err, kErrBuffer);
         __syncthreads();                                     // buffer and s_item reuse
@@ -862,7 +870,8 @@ __device__ __forceinline__ void run_item_flow(const GenCtx &g, uint32_t *buf, ui
             rel += words;
         }
     }
-    for (uint32_t j = tid; j < g.N; j += 64u * W) st[j] = buf[rel + j];   // state write-back (Sec. 8)
+    if (st)                                              // state write-back (Sec. 8)
+        for (uint32_t j = tid; j < g.N; j += 64u * W) st[j] = buf[rel + j];
 }
 
 template <int W, int CMAX>
@@ -916,11 +925,14 @@ __global__ void __launch_bounds__(64 * W, (64 * W) >= 512 ? 1 : 512 / (64 * W)) 
         bool ok = nc <= (uint32_t)CMAX && 2u * g.N + 2u * g.S + span + 32u <= B;
         if (ok) {
             uint32_t *st = a.state + gd.state_off;
-            for (uint32_t j = tid; j < g.N; j += T) buf[j] = st[j];
+            const bool piece = (w.flags & kItemPiece) != 0u;   // jump-ahead piece (Sec. 7)
+            const uint32_t *ld = piece ? a.jstate + w.src : st;
+            if (piece && !(w.flags & kItemLast)) st = nullptr;
+            for (uint32_t j = tid; j < g.N; j += T) buf[j] = ld[j];
             if (tid < (uint32_t)W) prog[tid] = 0u;
             __syncthreads();
             ok = dispatch_flow<W, CMAX>(nc, g, buf, B, w, a.segs + w.seg_begin, out, st, prog, a.err);
-            if (ok && tid == 0) gd.count += w.total;
+            if (ok && tid == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&gd.count), (unsigned long long)w.total);
         }
         if (!ok && tid == 0) atomicOr(a.err, kErrBuffer);
         __syncthreads();                                     // buffer, counters and s_item reuse

@@ -2,11 +2,13 @@
 // lists and launches.  Implements the C ABI declared in include/mtgp.h.
 #include "mtgp.h"
 #include "mtgp_internal.h"
+#include "mtgp_jump.h"
 
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <string>
 #include <vector>
@@ -169,6 +171,13 @@ struct mtgp_pool {
     cudaEvent_t ev_gen[2] = {nullptr, nullptr};
     cudaEvent_t ev_copy[2] = {nullptr, nullptr};
     mtgp_config cfg{};
+    uint64_t launches = 0;                 // kernels launched by generation calls
+    // jump-ahead (Sec. 7): polynomials, piece start states, walk scratch
+    JumpCache jc;
+    uint32_t *d_jstate = nullptr;
+    uint64_t jstate_words = 0;
+    uint32_t *d_seq = nullptr;
+    uint64_t seq_words = 0;
 };
 
 struct mtgp_state {
@@ -195,7 +204,9 @@ struct mtgp_graph {
 
 namespace {
 
-const mtgp_config kDefaultConfig = {128u, 0u, 0u, 256u, 0u, 0u};
+const mtgp_config kDefaultConfig = {128u, 0u, 0u, 256u, 0u, 0u, 0u, 0u};
+constexpr size_t kJumpStoreCap = (size_t)1 << 30;   // device bytes of cached jump polynomials
+constexpr uint64_t kSeqCap = 256ull << 20;           // walk scratch words per launch
 
 mtgp_status check_config(const mtgp_config &c)
 {
@@ -207,6 +218,9 @@ mtgp_status check_config(const mtgp_config &c)
     if (c.chunk < 32u || (c.chunk & (c.chunk - 1u)))
         return fail(MTGP_EINVAL, "chunk must be a power of two >= 32, got %u", c.chunk);
     if (c.buffer_words > 57344u) return fail(MTGP_EINVAL, "buffer_words must be <= 57344 (224 KiB)");
+    if (c.pieces > 64u) return fail(MTGP_EINVAL, "pieces must be <= 64");
+    if (c.piece_log2 != 0u && (c.piece_log2 < 10u || c.piece_log2 > 40u))
+        return fail(MTGP_EINVAL, "piece_log2 must be 0 or in [10, 40]");
     return MTGP_OK;
 }
 
@@ -259,6 +273,9 @@ mtgp_status ensure_upload_space(mtgp_pool *p, size_t bytes)
 struct Plan {
     std::vector<DevWork> work;
     std::vector<DevSeg> segs;
+    std::vector<DevJump> jobs;             // jump-ahead jobs starting the pieces
+    uint64_t jstate_words = 0, seq_words = 0;
+    uint32_t jmax_N = 0;
     uint32_t wmax = 0;
     uint32_t nmax = 0;
     uint64_t total = 0;
@@ -370,6 +387,152 @@ mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_
     return MTGP_OK;
 }
 
+// Grows the piece-state and walk scratch buffers (waiting for queued work
+// that may still read the old ones).
+mtgp_status ensure_jump_space(mtgp_pool *p, uint64_t jstate_words, uint64_t seq_words)
+{
+    if (jstate_words <= p->jstate_words && seq_words <= p->seq_words) return MTGP_OK;
+    if (p->used) CU(cudaEventSynchronize(p->ev_done), "cudaEventSynchronize");
+    if (jstate_words > p->jstate_words) {
+        if (p->d_jstate) CU(cudaFree(p->d_jstate), "cudaFree");
+        p->d_jstate = nullptr;
+        p->jstate_words = 0;
+        CU(cudaMalloc(&p->d_jstate, 4u * jstate_words), "cudaMalloc piece states");
+        p->jstate_words = jstate_words;
+    }
+    if (seq_words > p->seq_words) {
+        if (p->d_seq) CU(cudaFree(p->d_seq), "cudaFree");
+        p->d_seq = nullptr;
+        p->seq_words = 0;
+        const uint64_t w = std::max<uint64_t>(seq_words, seq_words + seq_words / 4u);
+        CU(cudaMalloc(&p->d_seq, 4u * w), "cudaMalloc walk scratch");
+        p->seq_words = w;
+    }
+    return MTGP_OK;
+}
+
+// Splits long blocked work items into pieces that run on separate blocks
+// (Sec. 7): piece m of an item of length n starts m L numbers into the
+// generator's stream, from the state F^(m L) s that the jump kernels compute
+// before the launch; the last piece writes the generator's state back.  The
+// pieces' outputs are exactly the item's, in the same places.
+mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
+{
+    const mtgp_config &c = p->cfg;
+    if (c.pieces == 1u || plan->work.empty()) return MTGP_OK;
+    const uint64_t min_piece = 1ull << (c.piece_log2 ? c.piece_log2 : 20u);
+    uint64_t kt = c.pieces;
+    if (!kt) {   // auto: enough blocks for about 16 per SM
+        const uint64_t target = 16ull * (uint64_t)std::max(p->sm_count, 1);
+        kt = std::min<uint64_t>(64u, (target + plan->work.size() - 1u) / plan->work.size());
+    }
+    if (kt < 2u) return MTGP_OK;
+    struct Cut {
+        uint32_t k;
+        uint64_t L;
+    };
+    std::vector<Cut> cut(plan->work.size(), Cut{0u, 0u});
+    std::vector<uint32_t> gl;
+    std::vector<std::pair<uint32_t, uint64_t>> need;
+    uint64_t seq_est = 0;
+    for (size_t w = 0; w < plan->work.size(); ++w) {
+        const DevWork &dw = plan->work[w];
+        const DevGen &g = p->host_gens[dw.gen];
+        // auto: a piece at least mexp N / 4 numbers long, so that its jump
+        // (about 0.7 mexp N word operations) stays a few per cent of its work
+        const uint64_t lmin = c.piece_log2 ? min_piece : std::max<uint64_t>(min_piece, (uint64_t)g.mexp * g.N / 4u);
+        if (dw.total < 2u * lmin) continue;
+        bool blocked = true;
+        for (uint32_t q = 0; q < dw.seg_count; ++q)
+            blocked = blocked && plan->segs[dw.seg_begin + q].chunk_log2 == kBlocked;
+        if (!blocked) continue;
+        uint64_t k = std::min<uint64_t>(kt, dw.total / lmin);
+        if (k < 2u) continue;
+        uint64_t L = (dw.total + k - 1u) / k;
+        L = (L + 63u) & ~63ull;
+        k = (dw.total + L - 1u) / L;
+        if (k < 2u) continue;
+        const uint64_t walk = (k - 1u) * (uint64_t)jump_seq_words(g.N, g.mexp + 1u) + jump_seq_words(g.N, 0u);
+        if (seq_est + walk > kSeqCap) continue;
+        seq_est += walk;
+        cut[w] = Cut{(uint32_t)k, L};
+        gl.push_back(dw.gen);
+        for (uint64_t m = 1; m < k; ++m) need.emplace_back(dw.gen, m * L);
+    }
+    if (gl.empty()) return MTGP_OK;
+    int st = jump_annihilate(p->jc, p->host_gens.data(), p->d_gens, p->d_state, gl.data(), gl.size(), s);
+    if (st != MTGP_OK) return (mtgp_status)st;
+    if (p->jc.dev_bytes > kJumpStoreCap) {
+        mtgp_status r = pool_sync(p);
+        if (r != MTGP_OK) return r;
+        jump_clear(p->jc, false);
+    }
+    st = jump_polys(p->jc, need);
+    if (st != MTGP_OK) return (mtgp_status)st;
+    std::vector<DevWork> work;
+    std::vector<DevSeg> segs;
+    uint64_t jst = 0, seq = 0;
+    for (size_t w = 0; w < plan->work.size(); ++w) {
+        const DevWork &dw = plan->work[w];
+        if (!cut[w].k) {
+            DevWork o = dw;
+            o.seg_begin = (uint32_t)segs.size();
+            segs.insert(segs.end(), plan->segs.begin() + dw.seg_begin,
+                        plan->segs.begin() + dw.seg_begin + dw.seg_count);
+            work.push_back(o);
+            continue;
+        }
+        const DevGen &g = p->host_gens[dw.gen];
+        const uint64_t L = cut[w].L;
+        for (uint32_t m = 0; m < cut[w].k; ++m) {
+            const uint64_t a = (uint64_t)m * L, b = std::min(a + L, dw.total);
+            DevWork pw{};
+            pw.gen = dw.gen;
+            pw.seg_begin = (uint32_t)segs.size();
+            pw.flags = kItemPiece | (m + 1u == cut[w].k ? kItemLast : 0u);
+            pw.total = b - a;
+            pw.src = jst;
+            uint64_t c0 = 0;
+            for (uint32_t q = 0; q < dw.seg_count; ++q) {
+                const DevSeg &sg = plan->segs[dw.seg_begin + q];
+                const uint64_t lo = std::max(a, c0), hi = std::min(b, c0 + sg.n);
+                if (lo < hi) {
+                    DevSeg o = sg;
+                    o.n = hi - lo;
+                    o.out_off = sg.out_off + (lo - c0);
+                    segs.push_back(o);
+                }
+                c0 += sg.n;
+            }
+            pw.seg_count = (uint32_t)(segs.size() - pw.seg_begin);
+            work.push_back(pw);
+            DevJump jb{};
+            if (m && !p->jc.polys.count({dw.gen, a})) return fail(MTGP_EINVAL, "jump polynomial missing");
+            const JumpPoly jp = m ? jump_poly(p->jc, dw.gen, a) : JumpPoly{};
+            jb.poly = jp.d;
+            jb.ncoef = jp.ncoef;
+            jb.src = g.state_off;
+            jb.dst = jst;
+            jb.seq = seq;
+            jb.gen = dw.gen;
+            jb.nseq = jump_seq_words(g.N, jb.ncoef);
+            jb.mode = kJumpStep;
+            plan->jobs.push_back(jb);
+            plan->jmax_N = std::max(plan->jmax_N, g.N);
+            jst += (g.N + 3u) & ~3u;
+            seq += jb.nseq;
+        }
+    }
+    plan->work.swap(work);
+    plan->segs.swap(segs);
+    plan->jstate_words = jst;
+    plan->seq_words = seq;
+    if (c.persistent)
+        std::stable_sort(plan->work.begin(), plan->work.end(),
+                         [](const DevWork &x, const DevWork &y) { return x.total > y.total; });
+    return MTGP_OK;
+}
+
 mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStream_t s)
 {
     if (plan.work.empty()) return MTGP_OK;
@@ -382,13 +545,27 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     // upload
     const size_t wbytes = plan.work.size() * sizeof(DevWork);
     const size_t sbytes = plan.segs.size() * sizeof(DevSeg);
-    mtgp_status st = ensure_upload_space(p, wbytes + sbytes);
+    const size_t jbytes = plan.jobs.size() * sizeof(DevJump);
+    mtgp_status st = ensure_upload_space(p, wbytes + sbytes + jbytes);
     if (st != MTGP_OK) return st;
+    if (!plan.jobs.empty()) {
+        st = ensure_jump_space(p, plan.jstate_words, plan.seq_words);
+        if (st != MTGP_OK) return st;
+    }
     std::memcpy(p->h_stage, plan.work.data(), wbytes);
     std::memcpy((char *)p->h_stage + wbytes, plan.segs.data(), sbytes);
-    CU(cudaMemcpyAsync(p->d_work, p->h_stage, wbytes + sbytes, cudaMemcpyHostToDevice, s), "upload work list");
+    std::memcpy((char *)p->h_stage + wbytes + sbytes, plan.jobs.data(), jbytes);
+    CU(cudaMemcpyAsync(p->d_work, p->h_stage, wbytes + sbytes + jbytes, cudaMemcpyHostToDevice, s),
+       "upload work list");
     CU(cudaEventRecord(p->ev_upload, s), "cudaEventRecord");
     p->upload_pending = true;
+    if (!plan.jobs.empty()) {   // start states of the pieces (Sec. 7)
+        const DevJump *jobs = (const DevJump *)((char *)p->d_work + wbytes + sbytes);
+        const uint32_t nj = (uint32_t)plan.jobs.size();
+        CU(launch_walk(p->d_gens, p->d_state, p->d_seq, jobs, nj, plan.jmax_N, s), "walk kernel launch");
+        CU(launch_jump_sum(p->d_gens, p->d_seq, p->d_jstate, jobs, nj, plan.jmax_N, s), "jump kernel launch");
+        p->launches += 2u;
+    }
     uint32_t grid = (uint32_t)plan.work.size();
     if (c.persistent) {
         CU(cudaMemsetAsync(p->d_ctl, 0, sizeof(unsigned), s), "reset work counter");
@@ -409,7 +586,9 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     a.nwork = (uint32_t)plan.work.size();
     a.buf_words = B;
     a.persistent = c.persistent;
+    a.jstate = p->d_jstate;
     CU(launch_generate(a, c.threads, c.form, qmax, grid, s), "generate kernel launch");
+    p->launches += 1u;
     CU(cudaEventRecord(p->ev_done, s), "cudaEventRecord");
     p->last_stream = s;
     p->used = true;
@@ -426,6 +605,8 @@ mtgp_status pool_run(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void
     if (st != MTGP_OK) return st;
     if (plan.total && !dev_out) return fail(MTGP_EINVAL, "dev_out is NULL");
     if (((uintptr_t)dev_out & 3u) != 0) return fail(MTGP_EINVAL, "dev_out must be 4-byte aligned");
+    st = split_plan(p, &plan, s);
+    if (st != MTGP_OK) return st;
     return launch_plan(p, plan, dev_out, s);
 }
 
@@ -508,6 +689,7 @@ mtgp_status mtgp_pool_create(const mtgp_params *ps, const uint32_t *gen_ids, con
     p->count = count;
     p->cfg = kDefaultConfig;
     p->host_gens.resize(count);
+    p->jc.ann.resize(count);
     uint64_t off = 0;
     for (uint32_t i = 0; i < count; ++i) {
         DevGen &g = p->host_gens[i];
@@ -572,7 +754,7 @@ mtgp_status mtgp_pool_info(const mtgp_pool *p, uint32_t *count, uint64_t *device
     if (count) *count = p->count;
     if (device_bytes)
         *device_bytes = sizeof(DevGen) * (uint64_t)p->count + 4ull * p->state_words + p->d_work_bytes +
-                        2ull * p->e2e_bytes;
+                        2ull * p->e2e_bytes + p->jc.dev_bytes + 4ull * (p->jstate_words + p->seq_words);
     return MTGP_OK;
 }
 
@@ -756,6 +938,7 @@ mtgp_status mtgp_pool_load(mtgp_pool *p, const void *host_buf, size_t bytes)
     CU(cudaMemcpy(p->d_state, (const char *)host_buf + 16 + sizeof(DevGen) * p->count, 4u * p->state_words,
                   cudaMemcpyHostToDevice),
        "load states");
+    jump_clear(p->jc, true);   // annihilators belong to the replaced states
     return MTGP_OK;
 }
 
@@ -765,6 +948,9 @@ void mtgp_pool_destroy(mtgp_pool *p)
     if (p->used && p->ev_done) cudaEventSynchronize(p->ev_done);
     if (p->copy_stream) cudaStreamSynchronize(p->copy_stream);
     if (p->upload_pending && p->ev_upload) cudaEventSynchronize(p->ev_upload);
+    jump_clear(p->jc, true);
+    cudaFree(p->d_jstate);
+    cudaFree(p->d_seq);
     cudaFree(p->d_gens);
     cudaFree(p->d_state);
     cudaFree(p->d_ctl);
@@ -1053,6 +1239,141 @@ mtgp_status mtgp_pool_errors(mtgp_pool *p, uint32_t *flags)
     CU(cudaMemcpy(flags, p->d_ctl + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost), "read error word");
     CU(cudaMemset(p->d_ctl + 1, 0, sizeof(uint32_t)), "clear error word");
     return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_launch_count(const mtgp_pool *p, uint64_t *launches)
+{
+    if (!p || !launches) return fail(MTGP_EINVAL, "NULL argument");
+    *launches = p->launches;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_jump(mtgp_pool *p, uint32_t i, uint64_t steps, void *stream)
+{
+    if (!p || i >= p->count) return fail(MTGP_EINVAL, "bad pool or generator index");
+    cudaStream_t s = (cudaStream_t)stream;
+    mtgp_status st = pool_busy_check(p, s);
+    if (st != MTGP_OK) return st;
+    if (steps == 0) return MTGP_OK;
+    int r = jump_annihilate(p->jc, p->host_gens.data(), p->d_gens, p->d_state, &i, 1u, s);
+    if (r != MTGP_OK) return (mtgp_status)r;
+    if (p->jc.dev_bytes > kJumpStoreCap) {
+        st = pool_sync(p);
+        if (st != MTGP_OK) return st;
+        jump_clear(p->jc, false);
+    }
+    r = jump_polys(p->jc, {{i, steps}});
+    if (r != MTGP_OK) return (mtgp_status)r;
+    const JumpPoly jp = jump_poly(p->jc, i, steps);
+    const DevGen &g = p->host_gens[i];
+    DevJump jb{};
+    jb.poly = jp.d;
+    jb.ncoef = jp.ncoef;
+    jb.src = g.state_off;
+    jb.dst = g.state_off;                 // in place: the walk reads the state first
+    jb.gen = i;
+    jb.nseq = jump_seq_words(g.N, jb.ncoef);
+    jb.mode = kJumpStep;
+    st = ensure_upload_space(p, sizeof jb);
+    if (st != MTGP_OK) return st;
+    st = ensure_jump_space(p, 0u, jb.nseq);
+    if (st != MTGP_OK) return st;
+    std::memcpy(p->h_stage, &jb, sizeof jb);
+    CU(cudaMemcpyAsync(p->d_work, p->h_stage, sizeof jb, cudaMemcpyHostToDevice, s), "upload jump job");
+    CU(launch_walk(p->d_gens, p->d_state, p->d_seq, (const DevJump *)p->d_work, 1u, g.N, s), "walk kernel launch");
+    CU(launch_jump_sum(p->d_gens, p->d_seq, p->d_state, (const DevJump *)p->d_work, 1u, g.N, s),
+       "jump kernel launch");
+    CU(cudaStreamSynchronize(s), "jump");
+    uint64_t pos = 0;
+    char *cnt = (char *)p->d_gens + sizeof(DevGen) * i + offsetof(DevGen, count);
+    CU(cudaMemcpy(&pos, cnt, sizeof pos, cudaMemcpyDeviceToHost), "read position");
+    pos += steps;
+    CU(cudaMemcpy(cnt, &pos, sizeof pos, cudaMemcpyHostToDevice), "write position");
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_state_jump(mtgp_state *s, uint64_t steps, void *stream)
+{
+    if (!s) return fail(MTGP_EINVAL, "state is NULL");
+    return mtgp_pool_jump(s->pool, 0u, steps, stream);
+}
+
+mtgp_status mtgp_pool_annihilator(mtgp_pool *p, uint32_t i, uint64_t *poly, uint32_t poly_words,
+                                  uint32_t *degree, void *stream)
+{
+    if (!p || i >= p->count || !degree) return fail(MTGP_EINVAL, "bad pool, index or NULL degree");
+    cudaStream_t s = (cudaStream_t)stream;
+    mtgp_status st = pool_busy_check(p, s);
+    if (st != MTGP_OK) return st;
+    const int r = jump_annihilate(p->jc, p->host_gens.data(), p->d_gens, p->d_state, &i, 1u, s);
+    if (r != MTGP_OK) return (mtgp_status)r;
+    const f2::Poly &a = p->jc.ann[i];
+    const int64_t d = f2::degree(a);
+    *degree = (uint32_t)std::max<int64_t>(d, 0);
+    if (!poly) return MTGP_OK;
+    const size_t need = (size_t)(*degree / 64u) + 1u;
+    if (poly_words < need) return fail(MTGP_EINVAL, "poly has %u words, need %zu", poly_words, need);
+    std::memset(poly, 0, sizeof(uint64_t) * poly_words);
+    std::copy(a.begin(), a.end(), poly);
+    return MTGP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+mtgp_status poly_out(const f2::Poly &r, uint64_t *out, uint32_t out_words, int64_t *deg)
+{
+    *deg = f2::degree(r);
+    const size_t need = *deg < 0 ? 1u : (size_t)(*deg / 64) + 1u;
+    if (out_words < need) return fail(MTGP_EINVAL, "output has %u words, need %zu", out_words, need);
+    std::memset(out, 0, sizeof(uint64_t) * out_words);
+    std::copy(r.begin(), r.end(), out);
+    return MTGP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mtgp_status mtgp_f2_minpoly(const uint64_t *bits, uint64_t n, uint64_t *out, uint32_t out_words, int64_t *deg)
+{
+    if ((!bits && n) || !out || !deg) return fail(MTGP_EINVAL, "NULL argument");
+    try {
+        return poly_out(n ? f2::minpoly(bits, n) : f2::Poly{1u}, out, out_words, deg);
+    } catch (const std::exception &) {
+        return fail(MTGP_ENOMEM, "host allocation");
+    }
+}
+
+mtgp_status mtgp_f2_mulmod(const uint64_t *a, uint32_t a_words, const uint64_t *b, uint32_t b_words,
+                           const uint64_t *m, uint32_t m_words, uint64_t *out, uint32_t out_words, int64_t *deg)
+{
+    if ((!a && a_words) || (!b && b_words) || !m || !out || !deg) return fail(MTGP_EINVAL, "NULL argument");
+    try {
+        const f2::Poly mp(m, m + m_words);
+        if (f2::degree(mp) < 1) return fail(MTGP_EINVAL, "modulus of degree < 1");
+        const f2::Modulus M = f2::make_modulus(mp);
+        f2::Poly x(a, a + a_words), y(b, b + b_words);
+        f2::reduce(x, M);
+        f2::reduce(y, M);
+        return poly_out(f2::mulmod(x, y, M), out, out_words, deg);
+    } catch (const std::exception &) {
+        return fail(MTGP_ENOMEM, "host allocation");
+    }
+}
+
+mtgp_status mtgp_f2_xpow_mod(uint64_t e, const uint64_t *m, uint32_t m_words, uint64_t *out, uint32_t out_words,
+                             int64_t *deg)
+{
+    if (!m || !out || !deg) return fail(MTGP_EINVAL, "NULL argument");
+    try {
+        const f2::Poly mp(m, m + m_words);
+        if (f2::degree(mp) < 1) return fail(MTGP_EINVAL, "modulus of degree < 1");
+        return poly_out(f2::xpow_mod(e, f2::make_modulus(mp)), out, out_words, deg);
+    } catch (const std::exception &) {
+        return fail(MTGP_ENOMEM, "host allocation");
+    }
 }
 
 }  // extern "C"

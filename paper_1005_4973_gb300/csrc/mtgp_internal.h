@@ -32,11 +32,16 @@ static_assert(sizeof(DevSeg) == 32, "DevSeg layout");
 constexpr uint32_t kBlocked = 0xFFFFFFFFu;
 
 // One work item: consecutive segments of one generator, run by one block.
+// A piece (flags & kItemPiece) is part of a generator's stream split across
+// blocks by jump-ahead (Sec. 7): it starts from the state at LaunchArgs::jstate
+// + src and writes the generator's state back only if it is the last piece.
 struct alignas(16) DevWork {
-    uint32_t gen, seg_begin, seg_count, rsv;
-    uint64_t total, rsv2;
+    uint32_t gen, seg_begin, seg_count, flags;
+    uint64_t total, src;
 };
 static_assert(sizeof(DevWork) == 32, "DevWork layout");
+constexpr uint32_t kItemPiece = 1u;
+constexpr uint32_t kItemLast = 2u;
 
 // Error bits the kernels may set in LaunchArgs::err.
 constexpr unsigned kErrBuffer = 1u;  // a generator did not fit the launch's shape or buffer
@@ -58,7 +63,29 @@ struct LaunchArgs {
     const uint32_t *nwork_dev;
     uint32_t *const *out_dev;           // shared buffer, >= 2N + S + 32 words for every item
     uint32_t persistent;
+    const uint32_t *jstate;             // start states of pieces (DevWork::src)
 };
+
+// One job of the jump kernels: walk the recursion (Sec. 3.6) from the state at
+// src for nseq words into the sequence scratch at seq, then XOR the states the
+// coefficients of g select (Sec. 7) into the destination at dst.
+struct alignas(16) DevJump {
+    const uint64_t *poly;         // g: bit i of word i/64 = coefficient of x^i
+    uint64_t src, dst, seq;       // word offsets: source state, destination, sequence (16-byte aligned)
+    uint32_t gen;
+    uint32_t nseq;                // sequence words walked (>= N)
+    uint32_t ncoef;               // coefficients of g; 0 copies the state
+    uint32_t mode;                // kJumpSum or kJumpStep
+};
+static_assert(sizeof(DevJump) == 48, "DevJump layout");
+constexpr uint32_t kJumpSum = 0u;   // destination = sum_i g_i F^i s (first word's r low bits unspecified)
+constexpr uint32_t kJumpStep = 1u;  // destination = F(sum_i g_i F^i s): with g = x^(J-1) mod psi, F^J s exactly
+constexpr uint32_t kJumpPad = 32u;  // sequence words walked past ncoef + N (window of the sum)
+
+cudaError_t launch_walk(const DevGen *gens, const uint32_t *src_base, uint32_t *seq_base, const DevJump *jobs,
+                        uint32_t njobs, uint32_t max_N, cudaStream_t s);
+cudaError_t launch_jump_sum(const DevGen *gens, const uint32_t *seq_base, uint32_t *dst_base, const DevJump *jobs,
+                            uint32_t njobs, uint32_t max_N, cudaStream_t s);
 
 // Generation kernels are compiled per block size T and per maximum slot
 // count QMAX: k_generate<T, QMAX> runs generators whose round size S = N - M

@@ -1,0 +1,150 @@
+// Jump-ahead kernels (Sec. 7).  A state s of the linear transition F
+// (Sec. 3.3) jumps J steps as F^J s = g(F) s, g = x^J mod psi with psi(F) s = 0;
+// g(F) s = sum_i g_i F^i s is the XOR of the windows x_i .. x_{i+N-1} of the
+// recursion's word sequence picked by g's coefficients.  Two kernels, one
+// block per job:
+//   k_walk      runs the recursion (Sec. 3.6, no tempering) from the job's
+//               state and writes the word sequence x_0 .. x_{nseq-1};
+//   k_jump_sum  XORs the selected windows, each thread owning R consecutive
+//               words of the sum in registers, reading 2R-word windows of the
+//               sequence for every R coefficients that select any.
+#include "mtgp_internal.h"
+
+namespace mtgp {
+
+namespace {
+
+constexpr uint32_t kJumpThreads = 256;
+
+uint32_t pow2_at_least(uint32_t x)
+{
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// One word of the recursion (Sec. 3.6): x_{N+i} from x_i, x_{i+1}, x_{i+M}.
+__device__ __forceinline__ uint32_t rec_word(uint32_t a0, uint32_t a1, uint32_t aM, uint32_t mask, uint32_t sh1,
+                                             uint32_t sh2, const uint32_t *tbl)
+{
+    uint32_t t = (a0 & mask) ^ a1;
+    t ^= t << sh1;
+    const uint32_t u = t ^ (aM >> sh2);
+    return u ^ tbl[u & 15u];
+}
+
+// Words in rounds of S = N - M, kept in a circular shared buffer of Rb >= N + S
+// words (a power of two): round i0 reads x_{i0} .. x_{i0+N-1} and writes
+// x_{i0+N} .. x_{i0+N+S-1}.
+__global__ void __launch_bounds__(kJumpThreads) k_walk(const DevGen *gens, const uint32_t *src_base,
+                                                       uint32_t *seq_base, const DevJump *jobs, uint32_t Rb)
+{
+    extern __shared__ __align__(16) uint32_t x[];
+    __shared__ uint32_t tbl[16];
+    const DevJump jb = jobs[blockIdx.x];
+    const DevGen &g = gens[jb.gen];
+    const uint32_t N = g.N, M = g.M, S = N - M, mask = g.mask, sh1 = g.sh1, sh2 = g.sh2, Rm = Rb - 1u;
+    const uint32_t tid = threadIdx.x, nseq = jb.nseq;
+    if (tid < 16u) tbl[tid] = g.rec[tid];
+    const uint32_t *src = src_base + jb.src;
+    uint32_t *seq = seq_base + jb.seq;
+    for (uint32_t j = tid; j < N; j += kJumpThreads) {
+        const uint32_t v = src[j];
+        x[j] = v;
+        if (j < nseq) seq[j] = v;
+    }
+    __syncthreads();
+    for (uint32_t i0 = 0; i0 + N < nseq; i0 += S) {
+        for (uint32_t c = tid; c < S; c += kJumpThreads) {
+            const uint32_t i = i0 + c;
+            const uint32_t v = rec_word(x[i & Rm], x[(i + 1u) & Rm], x[(i + M) & Rm], mask, sh1, sh2, tbl);
+            x[(i + N) & Rm] = v;
+            if (i + N < nseq) seq[i + N] = v;
+        }
+        __syncthreads();
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kJumpThreads) k_jump_sum(const DevGen *gens, const uint32_t *seq_base,
+                                                           uint32_t *dst_base, const DevJump *jobs)
+{
+    extern __shared__ __align__(16) uint32_t y[];
+    __shared__ uint32_t tbl[16];
+    const DevJump jb = jobs[blockIdx.x];
+    const DevGen &g = gens[jb.gen];
+    const uint32_t N = g.N, tid = threadIdx.x, j0 = tid * (uint32_t)R;
+    const uint32_t *x = seq_base + jb.seq;
+    uint32_t *dst = dst_base + jb.dst;
+    if (jb.ncoef == 0u) {                                    // J = 0: the state itself
+        for (uint32_t j = tid; j < N; j += kJumpThreads) dst[j] = x[j];
+        return;
+    }
+    if (tid < 16u) tbl[tid] = g.rec[tid];
+    uint32_t acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0u;
+    if (j0 < N) {
+        for (uint32_t i = 0; i < jb.ncoef; i += (uint32_t)R) {
+            const uint32_t cb =
+                (uint32_t)(__ldg(jb.poly + (i >> 6)) >> (i & 63u)) & (uint32_t)((1ull << R) - 1ull);
+            if (!cb) continue;
+            uint32_t v[2 * R];
+            const uint4 *p4 = reinterpret_cast<const uint4 *>(x + i + j0);
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) {
+                const uint4 t = __ldg(p4 + q);
+                v[4 * q] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
+            }
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                if ((cb >> u) & 1u) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] ^= v[u + r];
+                }
+            }
+        }
+    }
+    if (jb.mode == kJumpSum) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (j0 + (uint32_t)r < N) dst[j0 + r] = acc[r];
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (j0 + (uint32_t)r < N) y[j0 + r] = acc[r];
+    __syncthreads();
+    for (uint32_t j = tid; j + 1u < N; j += kJumpThreads) dst[j] = y[j + 1u];
+    if (tid == 0u) dst[N - 1u] = rec_word(y[0], y[1], y[g.M], g.mask, g.sh1, g.sh2, tbl);
+}
+
+}  // namespace
+
+cudaError_t launch_walk(const DevGen *gens, const uint32_t *src_base, uint32_t *seq_base, const DevJump *jobs,
+                        uint32_t njobs, uint32_t max_N, cudaStream_t s)
+{
+    if (!njobs) return cudaSuccess;
+    if (max_N < 3u || max_N > 4096u) return cudaErrorInvalidValue;
+    const uint32_t Rb = pow2_at_least(2u * max_N);              // >= N + S for every job
+    k_walk<<<njobs, kJumpThreads, Rb * sizeof(uint32_t), s>>>(gens, src_base, seq_base, jobs, Rb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jump_sum(const DevGen *gens, const uint32_t *seq_base, uint32_t *dst_base, const DevJump *jobs,
+                            uint32_t njobs, uint32_t max_N, cudaStream_t s)
+{
+    if (!njobs) return cudaSuccess;
+    if (max_N < 3u || max_N > 4096u) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)max_N * sizeof(uint32_t);
+    if (max_N <= 8u * kJumpThreads)
+        k_jump_sum<8><<<njobs, kJumpThreads, smem, s>>>(gens, seq_base, dst_base, jobs);
+    else
+        k_jump_sum<16><<<njobs, kJumpThreads, smem, s>>>(gens, seq_base, dst_base, jobs);
+    return cudaGetLastError();
+}
+
+}  // namespace mtgp

@@ -31,6 +31,53 @@ def mtgp_fill_probe(dev_buf, words: int, pattern: int = 0x9E3779B9, stream=None)
     L.check(L.LIB.mtgp_fill_probe(L.ptr(dev_buf), words, pattern, L.stream_handle(stream)))
 
 
+# -- F2[x] routines behind jump-ahead (coefficient arrays: index = power of x) --
+def poly_to_words(c) -> np.ndarray:
+    c = np.asarray(c, dtype=np.uint8) & 1
+    w = np.zeros(max(1, (c.size + 63) // 64), dtype=np.uint64)
+    for i in np.nonzero(c)[0]:
+        w[i // 64] |= np.uint64(1) << np.uint64(i % 64)
+    return w
+
+
+def poly_from_words(w, deg: int) -> np.ndarray:
+    if deg < 0:
+        return np.zeros(0, dtype=np.uint8)
+    w = np.asarray(w, dtype=np.uint64)
+    i = np.arange(deg + 1)
+    return ((w[i // 64] >> (i % 64).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
+
+
+def _u64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+def mtgp_f2_minpoly(bits) -> np.ndarray:
+    bits = np.asarray(bits, dtype=np.uint8) & 1
+    w = poly_to_words(bits) if bits.size else np.zeros(1, dtype=np.uint64)
+    out = np.zeros(bits.size // 64 + 3, dtype=np.uint64)
+    d = ctypes.c_int64()
+    L.check(L.LIB.mtgp_f2_minpoly(_u64p(w), bits.size, _u64p(out), out.size, ctypes.byref(d)))
+    return poly_from_words(out, d.value)
+
+
+def mtgp_f2_mulmod(a, b, m) -> np.ndarray:
+    aw, bw, mw = poly_to_words(a), poly_to_words(b), poly_to_words(m)
+    out = np.zeros(mw.size + 1, dtype=np.uint64)
+    d = ctypes.c_int64()
+    L.check(L.LIB.mtgp_f2_mulmod(_u64p(aw), aw.size, _u64p(bw), bw.size, _u64p(mw), mw.size, _u64p(out),
+                                 out.size, ctypes.byref(d)))
+    return poly_from_words(out, d.value)
+
+
+def mtgp_f2_xpow_mod(e: int, m) -> np.ndarray:
+    mw = poly_to_words(m)
+    out = np.zeros(mw.size + 1, dtype=np.uint64)
+    d = ctypes.c_int64()
+    L.check(L.LIB.mtgp_f2_xpow_mod(e, _u64p(mw), mw.size, _u64p(out), out.size, ctypes.byref(d)))
+    return poly_from_words(out, d.value)
+
+
 class Pool:
     """Device-resident generators (mtgp_pool_*)."""
 
@@ -105,6 +152,24 @@ class Pool:
         L.check(L.LIB.mtgp_pool_errors(self.handle, ctypes.byref(v)))
         return v.value
 
+    def launch_count(self) -> int:
+        v = ctypes.c_uint64()
+        L.check(L.LIB.mtgp_pool_launch_count(self.handle, ctypes.byref(v)))
+        return v.value
+
+    # -- jump-ahead (Sec. 7) ----------------------------------------------------
+    def jump(self, i: int, steps: int, stream=None) -> None:
+        L.check(L.LIB.mtgp_pool_jump(self.handle, i, steps, L.stream_handle(stream)))
+
+    def annihilator(self, i: int, stream=None) -> np.ndarray:
+        """Coefficients (uint8, index = power of x) of generator i's annihilating polynomial."""
+        d = ctypes.c_uint32()
+        L.check(L.LIB.mtgp_pool_annihilator(self.handle, i, None, 0, ctypes.byref(d), L.stream_handle(stream)))
+        words = np.zeros(d.value // 64 + 1, dtype=np.uint64)
+        L.check(L.LIB.mtgp_pool_annihilator(self.handle, i, words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                            words.size, ctypes.byref(d), L.stream_handle(stream)))
+        return poly_from_words(words, d.value)
+
     def info(self):
         c, b = ctypes.c_uint32(), ctypes.c_uint64()
         L.check(L.LIB.mtgp_pool_info(self.handle, ctypes.byref(c), ctypes.byref(b)))
@@ -139,6 +204,9 @@ class State:
         v = ctypes.c_uint64()
         L.check(L.LIB.mtgp_state_position(self.handle, ctypes.byref(v)))
         return v.value
+
+    def jump(self, steps: int, stream=None) -> None:
+        L.check(L.LIB.mtgp_state_jump(self.handle, steps, L.stream_handle(stream)))
 
     def save(self) -> bytes:
         n = ctypes.c_size_t()

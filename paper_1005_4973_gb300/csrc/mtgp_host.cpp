@@ -275,7 +275,7 @@ struct Plan {
     std::vector<DevSeg> segs;
     std::vector<DevJump> jobs;             // jump-ahead jobs starting the pieces
     uint64_t jstate_words = 0, seq_words = 0;
-    uint32_t jmax_N = 0;
+    uint32_t jmax_N = 0, jmax_nseq = 0, jmax_ncoef = 0;
     uint32_t wmax = 0;
     uint32_t nmax = 0;
     uint64_t total = 0;
@@ -519,6 +519,8 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
             jb.mode = kJumpStep;
             plan->jobs.push_back(jb);
             plan->jmax_N = std::max(plan->jmax_N, g.N);
+            plan->jmax_nseq = std::max(plan->jmax_nseq, jb.nseq);
+            plan->jmax_ncoef = std::max(plan->jmax_ncoef, jb.ncoef);
             jst += (g.N + 3u) & ~3u;
             seq += jb.nseq;
         }
@@ -548,8 +550,9 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     const size_t jbytes = plan.jobs.size() * sizeof(DevJump);
     mtgp_status st = ensure_upload_space(p, wbytes + sbytes + jbytes);
     if (st != MTGP_OK) return st;
+    const bool fused = jump_fused_fits(plan.jmax_N, plan.jmax_nseq, plan.jmax_ncoef);
     if (!plan.jobs.empty()) {
-        st = ensure_jump_space(p, plan.jstate_words, plan.seq_words);
+        st = ensure_jump_space(p, plan.jstate_words, fused ? 0u : plan.seq_words);
         if (st != MTGP_OK) return st;
     }
     std::memcpy(p->h_stage, plan.work.data(), wbytes);
@@ -562,9 +565,16 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     if (!plan.jobs.empty()) {   // start states of the pieces (Sec. 7)
         const DevJump *jobs = (const DevJump *)((char *)p->d_work + wbytes + sbytes);
         const uint32_t nj = (uint32_t)plan.jobs.size();
-        CU(launch_walk(p->d_gens, p->d_state, p->d_seq, jobs, nj, plan.jmax_N, s), "walk kernel launch");
-        CU(launch_jump_sum(p->d_gens, p->d_seq, p->d_jstate, jobs, nj, plan.jmax_N, s), "jump kernel launch");
-        p->launches += 2u;
+        if (fused) {
+            CU(launch_jump_fused(p->d_gens, p->d_state, p->d_jstate, jobs, nj, plan.jmax_N, plan.jmax_nseq,
+                                 plan.jmax_ncoef, s),
+               "jump kernel launch");
+            p->launches += 1u;
+        } else {
+            CU(launch_walk(p->d_gens, p->d_state, p->d_seq, jobs, nj, plan.jmax_N, s), "walk kernel launch");
+            CU(launch_jump_sum(p->d_gens, p->d_seq, p->d_jstate, jobs, nj, plan.jmax_N, s), "jump kernel launch");
+            p->launches += 2u;
+        }
     }
     uint32_t grid = (uint32_t)plan.work.size();
     if (c.persistent) {
@@ -1276,13 +1286,21 @@ mtgp_status mtgp_pool_jump(mtgp_pool *p, uint32_t i, uint64_t steps, void *strea
     jb.mode = kJumpStep;
     st = ensure_upload_space(p, sizeof jb);
     if (st != MTGP_OK) return st;
-    st = ensure_jump_space(p, 0u, jb.nseq);
+    const bool fused = jump_fused_fits(g.N, jb.nseq, jb.ncoef);
+    st = ensure_jump_space(p, 0u, fused ? 0u : jb.nseq);
     if (st != MTGP_OK) return st;
     std::memcpy(p->h_stage, &jb, sizeof jb);
     CU(cudaMemcpyAsync(p->d_work, p->h_stage, sizeof jb, cudaMemcpyHostToDevice, s), "upload jump job");
-    CU(launch_walk(p->d_gens, p->d_state, p->d_seq, (const DevJump *)p->d_work, 1u, g.N, s), "walk kernel launch");
-    CU(launch_jump_sum(p->d_gens, p->d_seq, p->d_state, (const DevJump *)p->d_work, 1u, g.N, s),
-       "jump kernel launch");
+    if (fused) {                          // in place: the block reads the whole state before writing
+        CU(launch_jump_fused(p->d_gens, p->d_state, p->d_state, (const DevJump *)p->d_work, 1u, g.N, jb.nseq,
+                             jb.ncoef, s),
+           "jump kernel launch");
+    } else {
+        CU(launch_walk(p->d_gens, p->d_state, p->d_seq, (const DevJump *)p->d_work, 1u, g.N, s),
+           "walk kernel launch");
+        CU(launch_jump_sum(p->d_gens, p->d_seq, p->d_state, (const DevJump *)p->d_work, 1u, g.N, s),
+           "jump kernel launch");
+    }
     CU(cudaStreamSynchronize(s), "jump");
     uint64_t pos = 0;
     char *cnt = (char *)p->d_gens + sizeof(DevGen) * i + offsetof(DevGen, count);

@@ -84,6 +84,11 @@ constexpr uint32_t kJumpPad = 32u;  // sequence words walked past ncoef + N (win
 
 cudaError_t launch_walk(const DevGen *gens, const uint32_t *src_base, uint32_t *seq_base, const DevJump *jobs,
                         uint32_t njobs, uint32_t max_N, cudaStream_t s);
+// Walk and sum in one kernel with the sequence in shared memory (no scratch),
+// when every job's sequence fits; the two kernels above otherwise.
+bool jump_fused_fits(uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef);
+cudaError_t launch_jump_fused(const DevGen *gens, const uint32_t *src_base, uint32_t *dst_base, const DevJump *jobs,
+                              uint32_t njobs, uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef, cudaStream_t s);
 cudaError_t launch_jump_sum(const DevGen *gens, const uint32_t *seq_base, uint32_t *dst_base, const DevJump *jobs,
                             uint32_t njobs, uint32_t max_N, cudaStream_t s);
 

@@ -122,7 +122,121 @@ __global__ void __launch_bounds__(kJumpThreads) k_jump_sum(const DevGen *gens, c
     if (tid == 0u) dst[N - 1u] = rec_word(y[0], y[1], y[g.M], g.mask, g.sh1, g.sh2, tbl);
 }
 
+// Walk and sum in one block, the sequence in shared memory: x (seq_cap
+// words), then y (the sum, max_N words), then g's coefficients (poly_cap
+// 32-bit words).  The sum splits the work two ways: G = ceil(N / R) groups of
+// R words times C = T / G slices of g's coefficients; slices XOR their partial
+// sums into y with shared atomics.
+template <int R, int T>
+__global__ void __launch_bounds__(T, 2) k_jump_fused(const DevGen *gens, const uint32_t *src_base,
+                                                    uint32_t *dst_base, const DevJump *jobs, uint32_t seq_cap,
+                                                    uint32_t max_N)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ uint32_t tbl[16];
+    uint32_t *x = sm, *y = sm + seq_cap, *cf = sm + seq_cap + max_N;
+    const DevJump jb = jobs[blockIdx.x];
+    const DevGen &g = gens[jb.gen];
+    const uint32_t N = g.N, M = g.M, S = N - M, mask = g.mask, sh1 = g.sh1, sh2 = g.sh2;
+    const uint32_t tid = threadIdx.x, ncoef = jb.ncoef;
+    uint32_t *dst = dst_base + jb.dst;
+    if (tid < 16u) tbl[tid] = g.rec[tid];
+    const uint32_t *src = src_base + jb.src;
+    for (uint32_t j = tid; j < N; j += T) {
+        x[j] = src[j];
+        y[j] = 0u;
+    }
+    const uint32_t cw = (ncoef + 31u) / 32u;
+    for (uint32_t w = tid; w < cw; w += T) cf[w] = (uint32_t)(jb.poly[w >> 1] >> (32u * (w & 1u)));
+    __syncthreads();
+    if (ncoef == 0u) {                                      // J = 0: the state itself
+        for (uint32_t j = tid; j < N; j += T) dst[j] = x[j];
+        return;
+    }
+    const uint32_t nseq = jb.nseq;
+    for (uint32_t i0 = 0; i0 + N < nseq; i0 += S) {
+        for (uint32_t c = tid; c < S; c += T) {
+            const uint32_t i = i0 + c;
+            if (i + N < nseq) x[i + N] = rec_word(x[i], x[i + 1u], x[i + M], mask, sh1, sh2, tbl);
+        }
+        __syncthreads();
+    }
+    const uint32_t G = (N + (uint32_t)R - 1u) / (uint32_t)R, C = T / G;
+    const uint32_t wg = tid % G, cs = tid / G, j0 = wg * (uint32_t)R;
+    if (cs < C) {
+        uint32_t acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0u;
+        const uint32_t ng = (ncoef + (uint32_t)R - 1u) / (uint32_t)R;
+        const uint32_t g0 = (uint32_t)((uint64_t)ng * cs / C), g1 = (uint32_t)((uint64_t)ng * (cs + 1u) / C);
+        for (uint32_t gi = g0; gi < g1; ++gi) {
+            const uint32_t i = gi * (uint32_t)R;
+            const uint32_t cb = (cf[i >> 5] >> (i & 31u)) & (uint32_t)((1ull << R) - 1ull);
+            if (!cb) continue;
+            uint32_t v[2 * R];
+            const uint4 *p4 = reinterpret_cast<const uint4 *>(x + i + j0);
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) {
+                const uint4 t = p4[q];
+                v[4 * q] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
+            }
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                if ((cb >> u) & 1u) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] ^= v[u + r];
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (j0 + (uint32_t)r < N && acc[r]) atomicXor(&y[j0 + r], acc[r]);
+    }
+    __syncthreads();
+    if (jb.mode == kJumpSum) {
+        for (uint32_t j = tid; j < N; j += T) dst[j] = y[j];
+        return;
+    }
+    for (uint32_t j = tid; j + 1u < N; j += T) dst[j] = y[j + 1u];
+    if (tid == 0u) dst[N - 1u] = rec_word(y[0], y[1], y[M], mask, sh1, sh2, tbl);
+}
+
+constexpr uint32_t kFusedThreads = 512;
+constexpr size_t kFusedSmemMax = 200u * 1024u;
+
+size_t fused_smem(uint32_t seq_cap, uint32_t max_N, uint32_t max_ncoef)
+{
+    return sizeof(uint32_t) * ((size_t)seq_cap + max_N + (max_ncoef + 31u) / 32u + 4u);
+}
+
 }  // namespace
+
+bool jump_fused_fits(uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef)
+{
+    return max_N <= 8u * kFusedThreads && fused_smem((max_nseq + 3u) & ~3u, max_N, max_ncoef) <= kFusedSmemMax;
+}
+
+cudaError_t launch_jump_fused(const DevGen *gens, const uint32_t *src_base, uint32_t *dst_base, const DevJump *jobs,
+                              uint32_t njobs, uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef, cudaStream_t s)
+{
+    if (!njobs) return cudaSuccess;
+    if (max_N < 3u || !jump_fused_fits(max_N, max_nseq, max_ncoef)) return cudaErrorInvalidValue;
+    const uint32_t seq_cap = (max_nseq + 3u) & ~3u;
+    const size_t smem = fused_smem(seq_cap, max_N, max_ncoef);
+    auto k = k_jump_fused<8, kFusedThreads>;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
+    if (smem + 64u > 48u * 1024u && cap == cudaStreamCaptureStatusNone) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<njobs, kFusedThreads, smem, s>>>(gens, src_base, dst_base, jobs, seq_cap, max_N);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_walk(const DevGen *gens, const uint32_t *src_base, uint32_t *seq_base, const DevJump *jobs,
                         uint32_t njobs, uint32_t max_N, cudaStream_t s)

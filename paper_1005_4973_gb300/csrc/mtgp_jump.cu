@@ -123,10 +123,51 @@ __global__ void __launch_bounds__(kJumpThreads) k_jump_sum(const DevGen *gens, c
 }
 
 // Walk and sum in one block, the sequence in shared memory: x (seq_cap
-// words), then y (the sum, max_N words), then g's coefficients (poly_cap
-// 32-bit words).  The sum splits the work two ways: G = ceil(N / R) groups of
-// R words times C = T / G slices of g's coefficients; slices XOR their partial
-// sums into y with shared atomics.
+// words), then y (the sum, max_N words), then g's coefficients (32-bit
+// words).  The sum splits the work two ways: a slice of WS = ceil(N / 32R)
+// warps covers the N words, R consecutive words per lane, and the block's
+// warps form C = warps / WS slices, each taking a contiguous share of g's
+// coefficients; slices XOR their partial sums into y with shared atomics.
+// Slices are whole warps, so the coefficient tests branch uniformly.  A lane
+// slides a 2R-word window along the sequence: for each R coefficients it
+// loads the next R words (R = 12: three 16-byte loads at a 48-byte lane
+// stride, which touch every bank exactly once per 8 lanes).
+template <int R, int T>
+__device__ __forceinline__ void sum_group(uint32_t (&acc)[R], const uint32_t (&lo)[R], const uint32_t (&hi)[R],
+                                          uint32_t cb)
+{
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        if ((cb >> u) & 1u) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] ^= (u + r < R) ? lo[u + r] : hi[u + r - R];
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void load_words(uint32_t (&v)[R], const uint32_t *p)
+{
+    const uint4 *p4 = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+    for (int q = 0; q < R / 4; ++q) {
+        const uint4 t = p4[q];
+        v[4 * q] = t.x;
+        v[4 * q + 1] = t.y;
+        v[4 * q + 2] = t.z;
+        v[4 * q + 3] = t.w;
+    }
+}
+
+// R coefficient bits starting at bit i of the 32-bit coefficient words.
+template <int R>
+__device__ __forceinline__ uint32_t coef_bits(const uint32_t *cf, uint32_t i)
+{
+    const uint32_t w = i >> 5, sh = i & 31u;
+    const uint32_t v = __funnelshift_r(cf[w], cf[w + 1u], sh);
+    return v & ((1u << R) - 1u);
+}
+
 template <int R, int T>
 __global__ void __launch_bounds__(T, 2) k_jump_fused(const DevGen *gens, const uint32_t *src_base,
                                                     uint32_t *dst_base, const DevJump *jobs, uint32_t seq_cap,
@@ -147,7 +188,8 @@ __global__ void __launch_bounds__(T, 2) k_jump_fused(const DevGen *gens, const u
         y[j] = 0u;
     }
     const uint32_t cw = (ncoef + 31u) / 32u;
-    for (uint32_t w = tid; w < cw; w += T) cf[w] = (uint32_t)(jb.poly[w >> 1] >> (32u * (w & 1u)));
+    for (uint32_t w = tid; w < cw + 1u; w += T)           // one zero word past the end
+        cf[w] = w < cw ? (uint32_t)(jb.poly[w >> 1] >> (32u * (w & 1u))) : 0u;
     __syncthreads();
     if (ncoef == 0u) {                                      // J = 0: the state itself
         for (uint32_t j = tid; j < N; j += T) dst[j] = x[j];
@@ -161,35 +203,27 @@ __global__ void __launch_bounds__(T, 2) k_jump_fused(const DevGen *gens, const u
         }
         __syncthreads();
     }
-    const uint32_t G = (N + (uint32_t)R - 1u) / (uint32_t)R, C = T / G;
-    const uint32_t wg = tid % G, cs = tid / G, j0 = wg * (uint32_t)R;
-    if (cs < C) {
-        uint32_t acc[R];
+    constexpr uint32_t kWarps = T / 32u;
+    const uint32_t WS = (N + 32u * (uint32_t)R - 1u) / (32u * (uint32_t)R), C = kWarps / WS;
+    const uint32_t warp = tid >> 5, cs = warp / WS;
+    const uint32_t j0 = ((warp % WS) * 32u + (tid & 31u)) * (uint32_t)R;
+    if (cs < C && j0 < N) {
+        uint32_t acc[R], va[R], vb[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = 0u;
         const uint32_t ng = (ncoef + (uint32_t)R - 1u) / (uint32_t)R;
         const uint32_t g0 = (uint32_t)((uint64_t)ng * cs / C), g1 = (uint32_t)((uint64_t)ng * (cs + 1u) / C);
-        for (uint32_t gi = g0; gi < g1; ++gi) {
-            const uint32_t i = gi * (uint32_t)R;
-            const uint32_t cb = (cf[i >> 5] >> (i & 31u)) & (uint32_t)((1ull << R) - 1ull);
-            if (!cb) continue;
-            uint32_t v[2 * R];
-            const uint4 *p4 = reinterpret_cast<const uint4 *>(x + i + j0);
-#pragma unroll
-            for (int q = 0; q < R / 2; ++q) {
-                const uint4 t = p4[q];
-                v[4 * q] = t.x;
-                v[4 * q + 1] = t.y;
-                v[4 * q + 2] = t.z;
-                v[4 * q + 3] = t.w;
-            }
-#pragma unroll
-            for (int u = 0; u < R; ++u) {
-                if ((cb >> u) & 1u) {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) acc[r] ^= v[u + r];
-                }
-            }
+        uint32_t gi = g0;
+        if (gi < g1) load_words<R>(va, x + gi * (uint32_t)R + j0);
+        while (gi < g1) {                                   // windows (va, vb), then (vb, va)
+            uint32_t i = gi * (uint32_t)R;
+            load_words<R>(vb, x + i + (uint32_t)R + j0);
+            sum_group<R, T>(acc, va, vb, coef_bits<R>(cf, i));
+            if (++gi >= g1) break;
+            i += (uint32_t)R;
+            load_words<R>(va, x + i + (uint32_t)R + j0);
+            sum_group<R, T>(acc, vb, va, coef_bits<R>(cf, i));
+            ++gi;
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -205,8 +239,11 @@ __global__ void __launch_bounds__(T, 2) k_jump_fused(const DevGen *gens, const u
 }
 
 constexpr uint32_t kFusedThreads = 512;
+constexpr uint32_t kFusedR = 12;
 constexpr size_t kFusedSmemMax = 200u * 1024u;
 
+// Sequence window: the sum reads up to word ncoef - 1 + R + (N rounded up to
+// a lane's R words) + R - 1 < ncoef + N + 3R.
 size_t fused_smem(uint32_t seq_cap, uint32_t max_N, uint32_t max_ncoef)
 {
     return sizeof(uint32_t) * ((size_t)seq_cap + max_N + (max_ncoef + 31u) / 32u + 4u);
@@ -216,7 +253,7 @@ size_t fused_smem(uint32_t seq_cap, uint32_t max_N, uint32_t max_ncoef)
 
 bool jump_fused_fits(uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef)
 {
-    return max_N <= 8u * kFusedThreads && fused_smem((max_nseq + 3u) & ~3u, max_N, max_ncoef) <= kFusedSmemMax;
+    return max_N <= kFusedR * kFusedThreads && fused_smem((max_nseq + 3u) & ~3u, max_N, max_ncoef) <= kFusedSmemMax;
 }
 
 cudaError_t launch_jump_fused(const DevGen *gens, const uint32_t *src_base, uint32_t *dst_base, const DevJump *jobs,
@@ -226,7 +263,7 @@ cudaError_t launch_jump_fused(const DevGen *gens, const uint32_t *src_base, uint
     if (max_N < 3u || !jump_fused_fits(max_N, max_nseq, max_ncoef)) return cudaErrorInvalidValue;
     const uint32_t seq_cap = (max_nseq + 3u) & ~3u;
     const size_t smem = fused_smem(seq_cap, max_N, max_ncoef);
-    auto k = k_jump_fused<8, kFusedThreads>;
+    auto k = k_jump_fused<kFusedR, kFusedThreads>;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return e;

@@ -208,7 +208,9 @@ def run_batched(torch, M, sample: int = 512):
     ms = e0.elapsed_time(e1) / steps
     assert graph.errors() == 0
     graph.close()
-    # one plain launch per generator (a one-request call each), first `sample` generators
+    # one plain launch per generator (a one-request call each, no jump-ahead
+    # pieces), first `sample` generators
+    pool.set_config(threads=128, persistent=0, pieces=1)
     sub = wl.requests[:sample]
     n_sub = sum(r[2] for r in sub)
     for r in sub[:8]:
@@ -231,6 +233,14 @@ def run_batched(torch, M, sample: int = 512):
                                     "note": "one launch per generator, first %d generators of C4" % len(sub)}}
 
 
+# Output arena of the served run.  A request holds 4 n bytes from admission
+# until it completes, about ceil(n / chunk) ticks later, so by Little's law the
+# arena must hold arrival rate x E[4 n ceil(n / chunk)] x tick time: about
+# 53 GB at 0.8 of the batched rate with chunk 2^22 and 3 ms ticks.  96 GiB
+# leaves headroom; 24 GiB capped the sustained rate near 190 Gnum/s.
+SERVE_ARENA = 96 << 30
+
+
 def run_served(torch, M, batched_gnums: float, fracs=(0.25, 0.5, 0.8), requests: int = 10000,
                warm: int = 1000):
     """C5: Poisson arrivals over 65536 resident generators at fractions of the
@@ -248,7 +258,7 @@ def run_served(torch, M, batched_gnums: float, fracs=(0.25, 0.5, 0.8), requests:
     for frac in fracs:
         rate = frac * batched_gnums * 1e9 / mean_len
         arrivals = WL.c5_arrivals(rate, warm + requests, pool_size=len(gens), seed=13 + int(100 * frac))
-        srv = M.Server(pool, arena_bytes=24 << 30, chunk=1 << 22, max_active=4096)
+        srv = M.Server(pool, arena_bytes=SERVE_ARENA, chunk=1 << 22, max_active=4096)
         lat, done = srv.run_trace(arrivals)
         st = srv.stats()
         srv.close()
@@ -265,7 +275,7 @@ def run_served(torch, M, batched_gnums: float, fracs=(0.25, 0.5, 0.8), requests:
     pool.close()
     return {"workload": "C5: 65536 resident generators (mexp mix as C4), Poisson arrivals, lengths "
                         "floor(2^U(8,26)), u32/f[0,1) 50/50, continuous batching",
-            "mean_len": mean_len, "chunk": 1 << 22, "max_active": 4096,
+            "mean_len": mean_len, "chunk": 1 << 22, "max_active": 4096, "arena_bytes": SERVE_ARENA,
             "latency": "device completion event minus host submission", "loop": "mtgp_server_run_trace (native)",
             "rates": results}
 

@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MTGP Gnum/s & HBM write GB/s vs peak (plain vs batched); served p50/p99 latency"
 KERNEL_SOURCES = ["paper_1005_4973_gb300/csrc/mtgp_device.cuh", "paper_1005_4973_gb300/csrc/mtgp_internal.h"]
-NCU_SUMMARY = os.path.join(ROOT, "profiles", "k_generate_c2_plain.md")
+NCU_SUMMARY = os.path.join(ROOT, "profiles", "k_generate_c2.md")
 
 
 def kernel_hash() -> str:
@@ -55,7 +55,9 @@ def measured_peaks():
 def workload(name: str, rank: int):
     from paper_1005_4973_gb300 import workloads as WL
     wl = {"c1": WL.c1, "c2": WL.c2, "c3": WL.c3, "c4": WL.c4,
-          "c2s": lambda: WL.c2(n=1 << 20)}[name]()
+          "c2s": lambda: WL.c2(n=1 << 20),
+          "c2m": lambda: WL.c2(n=1 << 22),
+          "paper": lambda: WL.paper()}[name]()
     if rank:
         for g in wl.gens:                  # distinct streams per rank
             g.gen_id += rank * 1_000_000
@@ -233,6 +235,43 @@ def run_batched(torch, M, sample: int = 512):
                                     "note": "one launch per generator, first %d generators of C4" % len(sub)}}
 
 
+# Sec. 4.4, Table 2: milliseconds for 5e7 numbers from 108 MTGP11213
+# generators on the GTX 260 and GT 120 (u32, f[1,2), f[0,1)).
+PAPER_MS = {"GTX 260": (4.7, 4.8, 5.0), "GT 120": (38.2, 38.9, 39.8)}
+
+
+def run_paper(torch, M, reps: int = 20):
+    """Sec. 4.4's workload: 5e7 numbers of each dtype from 108 MTGP11213
+    generators, default launch configuration; median CUDA-event time of
+    `reps` calls after warm-up."""
+    from paper_1005_4973_gb300 import workloads as WL
+    res = []
+    for dt, name in ((0, "u32"), (1, "f[1,2)"), (2, "f[0,1)")):
+        wl = WL.paper(dtype=dt)
+        ps = [M.mtgp_params_draw(g.mexp, g.param_seed, g.id) for g in wl.gens]
+        pool = M.Pool(ps, [g.gen_id for g in wl.gens], [g.seed for g in wl.gens])
+        out = torch.empty(wl.total_numbers, dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            pool.generate(wl.requests, out)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pool.generate(wl.requests, out)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        res.append({"dtype": name, "ms": ms, "gnums": wl.total_numbers / ms / 1e6,
+                    "paper_ms": {k: v[dt] for k, v in PAPER_MS.items()}})
+        pool.close()
+        del out
+    return {"workload": "Sec. 4.4: 5e7 numbers from 108 MTGP11213 generators per dtype, blocked",
+            "timing": "median of %d calls, CUDA events around the call (host planning included)" % reps,
+            "runs": res}
+
+
 # Output arena of the served run.  A request holds 4 n bytes from admission
 # until it completes, about ceil(n / chunk) ticks later, so by Little's law the
 # arena must hold arrival rate x E[4 n ceil(n / chunk)] x tick time: about
@@ -286,7 +325,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c2s"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c2s", "c2m", "paper"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -383,7 +422,7 @@ def main():
     avg_launch = statistics.mean(launch_ms)
     achieved = alg_bytes / (avg_launch * 1e-3) / 1e9
     traffic = None                                       # ncu DRAM bytes, scaled to this launch
-    if os.path.exists(NCU_SUMMARY) and args.workload in ("c2", "c2s"):
+    if os.path.exists(NCU_SUMMARY) and args.workload in ("c2", "c2s", "c2m"):
         fields = {}
         with open(NCU_SUMMARY) as f:
             for ln in f:
@@ -418,6 +457,8 @@ def main():
     if not args.no_extras and rank == 0 and world == 1 and args.workload == "c2":
         del out
         torch.cuda.empty_cache()
+        extras["paper_workload"] = run_paper(torch, M)
+        torch.cuda.empty_cache()
         extras["batched"] = run_batched(torch, M)
         torch.cuda.empty_cache()
         extras["served"] = run_served(torch, M, extras["batched"]["value"], requests=args.serve_requests)
@@ -432,6 +473,8 @@ def main():
                                     "c3": "C3: MTGP23209 + MTGP44497, 128 sets each x 2^26 f[0,1)",
                                     "c4": "C4: 8192 generators, mixed mexp, log-uniform 2^10..2^24, persistent",
                                     "c2s": "C2 at 2^20 numbers per generator (profiling size)",
+                                    "c2m": "C2 at 2^22 numbers per generator (profiling size, split into pieces)",
+                                    "paper": "Sec. 4.4: 5e7 f[0,1) numbers from 108 MTGP11213 generators",
                                     }[args.workload],
                        "generators": len(wl.gens), "numbers_per_step": total,
                        "bytes_written_per_step": 4 * total,

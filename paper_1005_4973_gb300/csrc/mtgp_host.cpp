@@ -427,6 +427,7 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
         kt = std::min<uint64_t>(64u, (target + plan->work.size() - 1u) / plan->work.size());
     }
     if (kt < 2u) return MTGP_OK;
+    const bool few = plan->work.size() < (size_t)std::max(p->sm_count, 1);
     struct Cut {
         uint32_t k;
         uint64_t L;
@@ -439,8 +440,12 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
         const DevWork &dw = plan->work[w];
         const DevGen &g = p->host_gens[dw.gen];
         // auto: a piece at least mexp N / 4 numbers long, so that its jump
-        // (about 0.7 mexp N word operations) stays a few per cent of its work
-        const uint64_t lmin = c.piece_log2 ? min_piece : std::max<uint64_t>(min_piece, (uint64_t)g.mexp * g.N / 4u);
+        // (about 0.7 mexp N word operations) stays a few per cent of its work;
+        // when the work items do not fill the SMs, pieces down to mexp N / 32
+        // (jumps then run on SMs that would otherwise idle)
+        const uint64_t lmin = c.piece_log2 ? min_piece
+                              : few ? std::max<uint64_t>(1u << 14, (uint64_t)g.mexp * g.N / 32u)
+                                    : std::max<uint64_t>(min_piece, (uint64_t)g.mexp * g.N / 4u);
         if (dw.total < 2u * lmin) continue;
         bool blocked = true;
         for (uint32_t q = 0; q < dw.seg_count; ++q)

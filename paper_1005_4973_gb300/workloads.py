@@ -18,6 +18,9 @@ Configurations (MTGP32; every output is 4 bytes):
   C5  served: 65536 resident generators (mexp mix as C4, numpy seed 11),
       Poisson arrivals, length floor(2^U(8, 26)), dtype uint32 / float [0,1)
       50/50, generator uniform.
+  paper  Sec. 4.4: 5e7 numbers of one dtype from 108 MTGP11213 generators
+      (parameter seeds 1..108, IDs 0..107, seed 1234), 462,963 each (the last
+      462,959), blocked.
 """
 from __future__ import annotations
 
@@ -76,6 +79,18 @@ def c2(n: int = 1 << 24, dtypes=(U32, F12, F01), count: int = 128) -> Workload:
             gens.append(GenSpec(11213, i + 1, i, i))
             reqs.append((len(gens) - 1, dt, n))
     return Workload("C2", gens, _blocked(reqs))
+
+
+def paper(dtype: int = F01, total: int = 50_000_000, count: int = 108) -> Workload:
+    """Sec. 4.4's speed measurement: 5e7 numbers of one dtype from 108
+    MTGP11213 generators with distinct parameter sets, split as evenly as
+    whole numbers allow."""
+    per = -(-total // count)
+    gens, reqs = [], []
+    for i in range(count):
+        gens.append(GenSpec(11213, i + 1, i, i))
+        reqs.append((i, dtype, min(per, total - i * per)))
+    return Workload("paper", gens, _blocked(reqs))
 
 
 def c3(mexps=(23209, 44497), n: int = 1 << 26, count: int = 128) -> Workload:

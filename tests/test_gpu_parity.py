@@ -357,9 +357,10 @@ def test_full_period_sets_on_gpu():
 
 
 # ----------------------------------------------------- full-size configs
-def _oracle_final_states(gens, n, dtype, nthreads=None):
+def _oracle_final_states(gens, n, dtype, nthreads=None, rows=None):
     """Oracle streams of many generators in chunks; returns final states and
-    the first `keep` outputs of each."""
+    the first `keep` outputs of each.  With rows (a device tensor, one row per
+    generator) every stream is also compared with its row in full."""
     keep = 1 << 16
     states, heads = [], []
     batch = 8
@@ -370,6 +371,12 @@ def _oracle_final_states(gens, n, dtype, nthreads=None):
             ps.append(p)
             sts.append(st)
         outs = O.generate_many(ps, sts, [n] * len(ps), [dtype] * len(ps), nthreads)
+        if rows is not None:
+            got = as_u32(rows[b:b + len(ps)])
+            for k, o in enumerate(outs):
+                if not np.array_equal(got[k], o):
+                    bad = np.nonzero(got[k] != o)[0]
+                    raise AssertionError(f"generator {b + k}: {bad.size} outputs differ, first at {bad[0]}")
         states += sts
         heads += [o[:keep].copy() for o in outs]
         del outs
@@ -377,8 +384,9 @@ def _oracle_final_states(gens, n, dtype, nthreads=None):
 
 
 def test_c2_full_size():
-    """C2: 128 sets x 2^24 x {u32, f12, f01}, the bench's launch (one block per
-    generator instance, 384 instances in one launch)."""
+    """C2: 128 sets x 2^24 x {u32, f12, f01}, the bench's launch (default
+    configuration: each instance split into jump-ahead pieces).  Every uint32
+    stream is compared in full; the float runs by the Sec. 6 closed forms."""
     wl = WL.c2()
     n = 1 << 24
     pool = lib_pool(wl.gens)
@@ -392,17 +400,12 @@ def test_c2_full_size():
     assert torch.equal(f12, (u >> 9) & 0x7FFFFF | 0x3F800000)
     ff = f12.view(torch.float32) - 1.0
     assert torch.equal(f01.view(torch.float32), ff)
-    # every generator's final state and first 2^16 numbers against the oracle (uint32 run)
-    states, heads = _oracle_final_states(wl.gens[:128], n, WL.U32)
-    uh = as_u32(u[:, : 1 << 16])
+    # every uint32 stream in full, every final state, against the oracle
+    states, heads = _oracle_final_states(wl.gens[:128], n, WL.U32, rows=u)
     for i in range(128):
-        assert np.array_equal(uh[i], heads[i]), i
         assert np.array_equal(pool.read_state(i), states[i]), i
         assert np.array_equal(pool.read_state(256 + i), states[i]), i
-    # two generators compared in full
-    for i in (0, 127):
-        (ref,), _ = oracle_stream(wl.gens[i], [(WL.U32, n)])
-        assert np.array_equal(as_u32(u[i]), ref)
+        assert pool.position(i) == n
 
 
 @pytest.mark.parametrize("mexp", [23209, 44497])
@@ -429,6 +432,28 @@ def test_c3_full_size(mexp):
         (ref,), st = oracle_stream(wl.gens[i], [(WL.F01, n)])
         assert np.array_equal(as_u32(f[i]), ref)
         assert np.array_equal(pool.read_state(i), st)
+
+
+@pytest.mark.parametrize("dtype", [WL.U32, WL.F12, WL.F01])
+def test_paper_workload_in_full(dtype):
+    """Sec. 4.4's workload (5e7 numbers from 108 MTGP11213 generators) in the
+    bench's launch (default configuration, pieces for the idle SMs), every
+    output and final state against the oracle."""
+    wl = WL.paper(dtype=dtype)
+    pool = lib_pool(wl.gens)
+    out = torch.empty(wl.total_numbers, dtype=torch.int32, device="cuda")
+    pool.generate(wl.requests, out)
+    torch.cuda.synchronize()
+    got = as_u32(out)
+    ps, sts = [], []
+    for g in wl.gens:
+        p, st = oracle_state(g)
+        ps.append(p)
+        sts.append(st)
+    refs = O.generate_many(ps, sts, [r[2] for r in wl.requests], [dtype] * len(ps))
+    for (g, _, n, off), ref in zip(wl.requests, refs):
+        assert np.array_equal(got[off:off + n], ref), g
+        assert np.array_equal(pool.read_state(g), sts[g]), g
 
 
 def test_c4_batched_sampled():

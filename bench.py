@@ -65,6 +65,13 @@ def workload(name: str, rank: int):
     return wl
 
 
+def max_over_ranks(torch, dist, x: float, device) -> float:
+    """The slowest rank's value (whole-job time is the max over ranks)."""
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled while running."""
 
@@ -280,8 +287,8 @@ def run_paper(torch, M, reps: int = 20):
 SERVE_ARENA = 96 << 30
 
 
-def run_served(torch, M, batched_gnums: float, fracs=(0.25, 0.5, 0.8), requests: int = 10000,
-               warm: int = 1000):
+def run_served(torch, M, batched_gnums: float, fracs=(0.25, 0.5, 0.8), requests: int = 50000,
+               warm: int = 2000):
     """C5: Poisson arrivals over 65536 resident generators at fractions of the
     measured batched rate, run by the library's native request loop; p50/p99
     latency (device completion minus host submission) over `requests` requests
@@ -333,7 +340,7 @@ def main():
     ap.add_argument("--ref-numbers", type=int, default=1 << 20, help="numbers per generator per reference step")
     ap.add_argument("--config", default="", help="JSON launch config overrides (threads, form, persistent, ...)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched (C4) and served (C5) measurements")
-    ap.add_argument("--serve-requests", type=int, default=10000, help="C5 requests timed per arrival rate")
+    ap.add_argument("--serve-requests", type=int, default=50000, help="C5 requests timed per arrival rate")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -409,9 +416,7 @@ def main():
     ms_total = e0.elapsed_time(e1)
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = max_over_ranks(torch, dist, ms_total, "cuda")
     clocks = sampler.summary(t_host0, t_host1) if sampler else None
 
     numbers_all = total * args.steps * world

@@ -52,6 +52,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+WORKLOAD_DESC = {
+    "c1": "C1: MTGP11213 x 1 generator x 2^20 u32",
+    "c2": "C2: MTGP11213, 128 sets x 2^24 x {u32, f[1,2), f[0,1)}, blocked",
+    "c3": "C3: MTGP23209 + MTGP44497, 128 sets each x 2^26 f[0,1)",
+    "c4": "C4: 8192 generators, mixed mexp, log-uniform 2^10..2^24, persistent",
+    "c2s": "C2 at 2^20 numbers per generator (profiling size)",
+    "c2m": "C2 at 2^22 numbers per generator (profiling size, split into pieces)",
+    "paper": "Sec. 4.4: 5e7 f[0,1) numbers from 108 MTGP11213 generators",
+}
+
+
 def workload(name: str, rank: int):
     from paper_1005_4973_gb300 import workloads as WL
     wl = {"c1": WL.c1, "c2": WL.c2, "c3": WL.c3, "c4": WL.c4,
@@ -185,7 +196,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gnum/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "config": {"workload": wl.name, "generators": len(ps)},
+        "data": "synthetic", "config": {"workload": WORKLOAD_DESC[args.workload], "generators": len(ps)},
         "cpu_baseline": {"value": value, "unit": "Gnum/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Gnum/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -473,14 +484,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "Gnum/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": {"c1": "C1: MTGP11213 x 1 generator x 2^20 u32",
-                                    "c2": "C2: MTGP11213, 128 sets x 2^24 x {u32, f[1,2), f[0,1)}, blocked",
-                                    "c3": "C3: MTGP23209 + MTGP44497, 128 sets each x 2^26 f[0,1)",
-                                    "c4": "C4: 8192 generators, mixed mexp, log-uniform 2^10..2^24, persistent",
-                                    "c2s": "C2 at 2^20 numbers per generator (profiling size)",
-                                    "c2m": "C2 at 2^22 numbers per generator (profiling size, split into pieces)",
-                                    "paper": "Sec. 4.4: 5e7 f[0,1) numbers from 108 MTGP11213 generators",
-                                    }[args.workload],
+            "config": {"workload": WORKLOAD_DESC[args.workload],
                        "generators": len(wl.gens), "numbers_per_step": total,
                        "bytes_written_per_step": 4 * total,
                        "l2": "outputs larger than the 129 MB L2 every step; no flush",

@@ -154,6 +154,28 @@ mtgp_status mtgp_params_draw(uint32_t mexp, uint64_t param_seed, uint32_t id, mt
  */
 mtgp_status mtgp_params_validate(const mtgp_params *p);
 
+/*
+ * Recursion-parameter search of MTGPDC (Sec. 5) on the host cores: candidates
+ * t = 0, 1, ... are mtgp_params_draw(mexp, seed0 + t, id) (ID embedded in R,
+ * R4 + I invertible, sh1 = 13, sh2 = 4, M in Sec. 5's range).  A candidate is
+ * accepted when the Berlekamp-Massey polynomial of the MSB sequence of 2 mexp
+ * words of its recursion (from a SplitMix64-filled state) has degree mexp and
+ * is irreducible -- then it is the characteristic polynomial of the
+ * transition F and primitive (mexp a Mersenne exponent), so the period is
+ * 2^mexp - 1 (Sec. 3.3).  Irreducibility: x^(2^mexp) = x mod phi and no root
+ * in F2, with an early gcd against prod_{k <= 40} (x^(2^k) - x).  Returns the
+ * smallest accepted t (whatever the thread count): the set in *out, seed0 + t
+ * in *found_seed, t + 1 in *tries, and, if charpoly is not NULL, phi (bit j of
+ * word j/64 = coefficient of x^j; charpoly_words >= mexp / 64 + 1).
+ * threads = 0 uses every host core.  MTGP_EINVAL if none of max_tries
+ * candidates qualifies.  The tempering table is drawn, not searched (the
+ * k(v) search of Sec. 5 is not implemented).  About a minute of 16 cores for
+ * mexp 11213; the cost grows roughly as mexp^3.
+ */
+mtgp_status mtgp_params_search(uint32_t mexp, uint64_t seed0, uint32_t id, uint64_t max_tries, uint32_t threads,
+                               mtgp_params *out, uint64_t *found_seed, uint64_t *tries, uint64_t *charpoly,
+                               uint32_t charpoly_words);
+
 /* ---- single generator (Sec. 8 host/kernel flow) --------------------------- */
 
 /*

@@ -184,6 +184,11 @@ Modulus make_modulus(const Poly &m0)
         if (sh > 56u) v |= row[w + 1u] << (64u - sh);
         M.inv[v & 0xFFu] = (uint8_t)c;
     }
+    const size_t nr = M.np + 1u;
+    M.P8.assign(8u * 256u * nr, 0u);
+    for (unsigned j = 0; j < 8u; ++j)
+        for (unsigned c = 1; c < 256u; ++c)
+            xor_shifted(&M.P8[((size_t)j * 256u + c) * nr], &M.P[(size_t)c * M.np], M.np - 1u, 8u * j);
     return M;
 }
 
@@ -199,10 +204,14 @@ void reduce(Poly &a, const Modulus &M)
     const int64_t da = degree(a);
     if (da < (int64_t)M.D) return;
     a.resize(std::max(a.size(), (size_t)(((uint64_t)da + 8u) >> 6) + M.np + 2u), 0u);
+    const size_t nr = M.np + 1u;
     for (int64_t t = (int64_t)M.D + (da - (int64_t)M.D) / 8 * 8; t >= (int64_t)M.D; t -= 8) {
         const uint32_t c = byte_at(a, (uint64_t)t);
         if (!c) continue;
-        xor_shifted(a.data(), &M.P[(size_t)M.inv[c] * M.np], M.np - 1u, (uint64_t)t - M.D);
+        const uint64_t sft = (uint64_t)t - M.D;               // a multiple of 8
+        const uint64_t *row = &M.P8[((size_t)((sft >> 3) & 7u) * 256u + M.inv[c]) * nr];
+        uint64_t *d = a.data() + (sft >> 6);
+        for (size_t k = 0; k < nr; ++k) d[k] ^= row[k];
     }
     a.resize((size_t)((M.D + 63u) >> 6));
     trim(a);
@@ -234,6 +243,27 @@ Poly mulx_mod(Poly a, const Modulus &M)
     for (size_t w = a.size() - 1u; w > 0; --w) a[w] = (a[w] << 1) | (a[w - 1u] >> 63);
     a[0] <<= 1;
     reduce(a, M);
+    return a;
+}
+
+// Euclid's algorithm, word-level: the remainder step XORs b shifted under
+// a's leading term until deg a < deg b.
+Poly gcd(Poly a, Poly b)
+{
+    trim(a);
+    trim(b);
+    while (!b.empty()) {
+        int64_t da = degree(a);
+        const int64_t db = degree(b);
+        while (da >= db) {
+            a.resize(std::max(a.size(), (size_t)((uint64_t)(da - db) / 64u) + b.size() + 1u), 0u);
+            xor_shifted(a.data(), b.data(), b.size(), (uint64_t)(da - db));
+            trim(a);
+            da = degree(a);
+            if (da < 0) break;
+        }
+        a.swap(b);
+    }
     return a;
 }
 

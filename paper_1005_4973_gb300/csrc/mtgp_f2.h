@@ -34,6 +34,9 @@ struct Modulus {
     size_t np = 0;                        // words per table row
     std::vector<uint64_t> P;              // P[c] = c(x) * m(x), c < 256
     uint8_t inv[256] = {};                // top byte of P[c] -> c
+    // P[c] shifted left by 8 j bits (j = 0 .. 7), np + 1 words per row, so
+    // that every reduction step XORs whole words
+    std::vector<uint64_t> P8;
 };
 Modulus make_modulus(const Poly &m);
 void reduce(Poly &a, const Modulus &M);
@@ -41,6 +44,7 @@ Poly mulmod(const Poly &a, const Poly &b, const Modulus &M);
 Poly sqrmod(const Poly &a, const Modulus &M);
 Poly mulx_mod(Poly a, const Modulus &M);  // x * a mod m
 Poly xpow_mod(uint64_t e, const Modulus &M);
+Poly gcd(Poly a, Poly b);                 // monic greatest common divisor
 
 }  // namespace f2
 }  // namespace mtgp

@@ -23,6 +23,31 @@ def mtgp_params_draw(mexp: int, param_seed: int, gen_id: int) -> mtgp_params:
     return p
 
 
+def mtgp_params_search(mexp: int, seed0: int, gen_id: int, max_tries: int = 1 << 20, threads: int = 0):
+    """Sec. 5 recursion-parameter search; returns (params, found_seed, tries,
+    characteristic polynomial as a coefficient array)."""
+    p = mtgp_params()
+    found, tries = ctypes.c_uint64(), ctypes.c_uint64()
+    words = np.zeros(mexp // 64 + 1, dtype=np.uint64)
+    L.check(L.LIB.mtgp_params_search(mexp, seed0, gen_id, max_tries, threads, ctypes.byref(p), ctypes.byref(found),
+                                     ctypes.byref(tries), words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                     words.size))
+    return p, found.value, tries.value, poly_from_words(words, mexp)
+
+
+def mtgpdc_record(p: mtgp_params, charpoly) -> str:
+    """One comma-separated record of a searched set, with the additional data
+    Sec. 5 lists: SHA1 of the characteristic polynomial (its coefficients as
+    a string of '0'/'1' from x^0 upward) and its number of nonzero terms.
+    (The dimension defect needs the tempering search, which is not done.)"""
+    import hashlib
+    c = np.asarray(charpoly, dtype=np.uint8)
+    sha = hashlib.sha1("".join("1" if v else "0" for v in c).encode()).hexdigest()
+    fields = [p.mexp, p.N, p.pos, p.sh1, p.sh2, p.id] + [f"{v:08x}" for v in p.rec_tbl] + \
+             [f"{v:08x}" for v in p.tmp_tbl] + [sha, int(c.sum())]
+    return ",".join(str(f) for f in fields)
+
+
 def mtgp_params_validate(p: mtgp_params) -> None:
     L.check(L.LIB.mtgp_params_validate(ctypes.byref(p)))
 

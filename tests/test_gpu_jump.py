@@ -215,3 +215,23 @@ def test_checkpoint_load_forgets_annihilators():
     torch.cuda.synchronize()
     reqs = [(0, 0, 100000, 0), (1, 0, 100000, 100000)]
     _check(gens, reqs, as_u32(out), pool)
+
+
+def test_searched_full_period_set_on_the_gpu():
+    """A set from the Sec. 5 search (mexp 4423): its generation matches the
+    oracle, and the annihilator the GPU walk finds for a seeded state is the
+    searched characteristic polynomial itself (irreducible, so every nonzero
+    state has it)."""
+    import paper_1005_4973_gb300 as M
+    p, seed, _, phi = M.mtgp_params_search(4423, 1, 0)
+    pool = M.Pool([p, p], [0, 1], [77, 78])
+    pool.set_config(pieces=4, piece_log2=12)
+    assert np.array_equal(pool.annihilator(0), phi)
+    assert np.array_equal(pool.annihilator(1), phi)
+    out = torch.zeros(100000, dtype=torch.int32, device="cuda")
+    pool.generate([(0, 2, 100000, 0)], out)
+    torch.cuda.synchronize()
+    op = O.params_draw(4423, seed, 0)
+    st = O.seed_state(op, 0, 77)
+    assert np.array_equal(as_u32(out), O.generate(op, st, 100000, 2))
+    assert np.array_equal(pool.read_state(0), st)

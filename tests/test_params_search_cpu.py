@@ -56,7 +56,7 @@ def test_search_limits_and_record(M):
     assert rec[0] == "89" and len(rec) == 6 + 32 + 2 and len(rec[-2]) == 40 and int(rec[-1]) == int(phi.sum())
 
 
-@pytest.mark.slow
+@pytest.mark.manual
 def test_full_size_mtgp11213_search(M):
     """A full-size search (about a minute of 16 cores): the polynomial has
     degree 11213, the oracle's irreducibility test agrees, and it annihilates

@@ -210,7 +210,7 @@ def run_batched(torch, M, sample: int = 512):
     wl = WL.c4()
     ps = [M.mtgp_params_draw(g.mexp, g.param_seed, g.id) for g in wl.gens]
     pool = M.Pool(ps, [g.gen_id for g in wl.gens], [g.seed for g in wl.gens])
-    pool.set_config(threads=256, persistent=1)
+    pool.set_config(threads=128, persistent=1)
     total = wl.total_numbers
     out = torch.empty(total, dtype=torch.int32, device="cuda")
     graph = M.Graph(pool, max_items=len(wl.gens))
@@ -247,7 +247,7 @@ def run_batched(torch, M, sample: int = 512):
                         "floor(2^U(10,24)), u32/f[0,1) alternating, blocked",
             "value": total / (ms * 1e-3) / 1e9, "unit": "Gnum/s", "ms_per_launch": ms,
             "hbm_write_gbs": 4 * total / (ms * 1e-3) / 1e9, "numbers": total,
-            "form": "one graph-captured persistent launch (256 threads, longest first)",
+            "form": "one graph-captured persistent launch (128 threads, longest first)",
             "plain_per_generator": {"value": n_sub / (ms_plain * 1e-3) / 1e9, "unit": "Gnum/s",
                                     "generators": len(sub), "launches": len(sub),
                                     "note": "one launch per generator, first %d generators of C4" % len(sub)}}
@@ -374,7 +374,7 @@ def main():
     wl = workload(args.workload, rank)
     ps = [M.mtgp_params_draw(g.mexp, g.param_seed, g.id) for g in wl.gens]
     pool = M.Pool(ps, [g.gen_id for g in wl.gens], [g.seed for g in wl.gens])
-    if args.workload == "c4":
+    if args.workload in ("c3", "c4"):
         pool.set_config(persistent=1)
     if args.config:
         pool.set_config(**json.loads(args.config))

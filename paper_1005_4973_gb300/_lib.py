@@ -11,6 +11,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_build", "libmtgp.so")
 
@@ -180,12 +182,27 @@ def stream_handle(stream) -> int | None:
     return stream.cuda_stream
 
 
+# numpy view of mtgp_request (same field order, sizes and padding)
+REQUEST_DTYPE = np.dtype([("gen", "<u4"), ("dtype", "<u4"), ("n", "<u8"), ("out_offset", "<u8")])
+
+
 def requests_array(reqs) -> ctypes.Array:
-    """List of (gen, dtype, n, out_offset) tuples or mtgp_request -> C array."""
-    arr = (mtgp_request * max(len(reqs), 1))()
-    for i, r in enumerate(reqs):
-        if isinstance(r, mtgp_request):
-            arr[i] = r
-        else:
-            arr[i] = mtgp_request(*[int(v) for v in r])
-    return arr
+    """(gen, dtype, n, out_offset) rows -- a list of tuples, an (n, 4) integer
+    array, a REQUEST_DTYPE array or mtgp_request objects -- as a C array of
+    mtgp_request.  Rows are converted column-wise by numpy, so a call with
+    thousands of requests does not pay a Python loop."""
+    n = len(reqs)
+    if isinstance(reqs, np.ndarray) and reqs.dtype == REQUEST_DTYPE:
+        a = np.ascontiguousarray(reqs) if n else np.zeros(1, dtype=REQUEST_DTYPE)
+    else:
+        a = np.zeros(max(n, 1), dtype=REQUEST_DTYPE)
+        if n and isinstance(reqs[0], mtgp_request):
+            for i, r in enumerate(reqs):
+                a[i] = (r.gen, r.dtype, r.n, r.out_offset)
+        elif n:
+            m = np.asarray(reqs, dtype=np.uint64).reshape(n, 4)
+            a["gen"][:n] = m[:, 0]
+            a["dtype"][:n] = m[:, 1]
+            a["n"][:n] = m[:, 2]
+            a["out_offset"][:n] = m[:, 3]
+    return (mtgp_request * len(a)).from_buffer(a)

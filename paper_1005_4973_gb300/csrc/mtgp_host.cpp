@@ -372,7 +372,7 @@ mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_
     }
     uint32_t B = c.buffer_words;
     if (!B) {
-        uint32_t per_sm = c.persistent ? (c.blocks_per_sm ? c.blocks_per_sm : 2u)
+        uint32_t per_sm = c.persistent ? (c.blocks_per_sm ? c.blocks_per_sm : 6u)
                                        : (uint32_t)std::min<size_t>(8, (items + p->sm_count - 1) / (size_t)p->sm_count);
         per_sm = std::max(per_sm, 1u);
         const uint32_t budget = std::min(57344u, (uint32_t)((227u * 1024u / per_sm - 1024u) / 4u));
@@ -421,11 +421,12 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
     const mtgp_config &c = p->cfg;
     if (c.pieces == 1u || plan->work.empty()) return MTGP_OK;
     const uint64_t min_piece = 1ull << (c.piece_log2 ? c.piece_log2 : 20u);
-    uint64_t kt = c.pieces;
-    if (!kt) {   // auto: enough blocks for about 16 per SM
-        const uint64_t target = 16ull * (uint64_t)std::max(p->sm_count, 1);
-        kt = std::min<uint64_t>(64u, (target + plan->work.size() - 1u) / plan->work.size());
-    }
+    // auto: pieces of about Lt = total / (16 SMs) numbers, so that the launch
+    // has about 16 equal shares of work per SM and long items stop setting its
+    // tail; explicit: up to `pieces` per item
+    const uint64_t kt = c.pieces ? c.pieces : 64u;
+    const uint64_t Lt = c.pieces ? 0u : (plan->total + 16ull * (uint64_t)std::max(p->sm_count, 1) - 1u) /
+                                           (16ull * (uint64_t)std::max(p->sm_count, 1));
     if (kt < 2u) return MTGP_OK;
     const bool few = plan->work.size() < (size_t)std::max(p->sm_count, 1);
     struct Cut {
@@ -452,6 +453,7 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
             blocked = blocked && plan->segs[dw.seg_begin + q].chunk_log2 == kBlocked;
         if (!blocked) continue;
         uint64_t k = std::min<uint64_t>(kt, dw.total / lmin);
+        if (Lt) k = std::min<uint64_t>(k, (dw.total + Lt - 1u) / Lt);
         if (k < 2u) continue;
         uint64_t L = (dw.total + k - 1u) / k;
         L = (L + 63u) & ~63ull;
@@ -1056,14 +1058,15 @@ mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
     if (st != MTGP_OK) return st;
     const mtgp_config orig = p->cfg;
     std::vector<mtgp_config> cands;
-    for (uint32_t form : {0u, 1u, 2u})
-        for (uint32_t threads : {32u, 64u, 128u, 256u, 512u, 1024u})
-            for (uint32_t pers : {0u, 1u})
-                for (uint32_t bps : {0u, 1u, 2u, 3u, 4u, 6u, 8u}) {
-                    if (!pers && bps) continue;
-                    if (!threads_supported(threads, form)) continue;
-                    cands.push_back(mtgp_config{threads, pers, bps, orig.chunk, 0u, form});
-                }
+    for (uint32_t pieces : {0u, 1u})                     // jump-ahead pieces: auto, or none
+        for (uint32_t form : {0u, 1u, 2u})
+            for (uint32_t threads : {32u, 64u, 128u, 256u, 512u, 1024u})
+                for (uint32_t pers : {0u, 1u})
+                    for (uint32_t bps : {0u, 1u, 2u, 3u, 4u, 6u, 8u}) {
+                        if (!pers && bps) continue;
+                        if (!threads_supported(threads, form)) continue;
+                        cands.push_back(mtgp_config{threads, pers, bps, orig.chunk, 0u, form, pieces, 0u});
+                    }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0), "cudaEventCreate");
     CU(cudaEventCreate(&e1), "cudaEventCreate");
@@ -1087,8 +1090,12 @@ mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     p->cfg = best_c;
+    // psi found while tuning annihilates the restored (earlier) states as well:
+    // psi(F) F^k s = 0 and F is invertible (R4 + I invertible, Sec. 5)
+    const std::vector<f2::Poly> ann = p->jc.ann;
     st = mtgp_pool_load(p, ckpt.data(), bytes);
     if (st != MTGP_OK) return st;
+    p->jc.ann = ann;
     if (best) *best = best_c;
     if (best_ms) *best_ms = best_t;
     return MTGP_OK;

@@ -68,12 +68,21 @@ struct DevBuf {
     ~DevBuf() { if (p) cudaFree(p); }
 };
 
-// Masks of the functional, one per pass (a pass that finds nothing new
-// switches to the next).
-constexpr uint32_t kMasks[] = {0xFFFFFFFFu, 0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu,
-                               0x80000000u, 0x00000001u, 0x12345678u, 0x9ABCDEF0u, 0x00010000u, 0x7FFFFFFFu,
-                               0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u};
-constexpr int kPasses = (int)(sizeof kMasks / sizeof kMasks[0]);
+// Mask of the functional of pass k: parities of mixes first, then every
+// single bit of the word.  A pass leaves a remainder whose sequence under its
+// functional is zero, and later passes keep it zero (they apply polynomials in
+// F to the remainder), so after the 32 single-bit passes every coordinate of
+// every state on the remainder's orbit is zero -- the state words x_1 ..
+// x_{N-1} directly, and the masked bits of x_0 through x_N, which the
+// recursion maps injectively (R4 + I invertible) -- and the remainder is 0.
+constexpr uint32_t kMixMasks[] = {0xFFFFFFFFu, 0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
+constexpr int kMixes = (int)(sizeof kMixMasks / sizeof kMixMasks[0]);
+constexpr int kPasses = kMixes + 32;
+
+uint32_t pass_mask(int k)
+{
+    return k < kMixes ? kMixMasks[k] : 1u << (k - kMixes);
+}
 
 }  // namespace
 
@@ -151,7 +160,7 @@ int jump_annihilate(JumpCache &jc, const DevGen *hg, const DevGen *d_gens, const
             JCU(cudaMemcpyAsync(host_seq.data(), d_seq.p, 4ull * words, cudaMemcpyDeviceToHost, s), "read walk");
             JCU(cudaStreamSynchronize(s), "walk");
             // minimal polynomial of the functional's sequence, per generator
-            const uint32_t fmask = kMasks[pass];
+            const uint32_t fmask = pass_mask(pass);
             std::vector<f2::Poly> phi(act.size());
             std::atomic<bool> oom{false};
             parallel_for(act.size(), [&](size_t a) {

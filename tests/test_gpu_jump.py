@@ -235,3 +235,21 @@ def test_searched_full_period_set_on_the_gpu():
     st = O.seed_state(op, 0, 77)
     assert np.array_equal(as_u32(out), O.generate(op, st, 100000, 2))
     assert np.array_equal(pool.read_state(0), st)
+
+
+def test_autotune_leaves_streams_untouched_and_keeps_parity():
+    """mtgp_autotune times candidate configurations (forms, block sizes,
+    persistence, pieces on/off) and restores every state afterwards: the
+    positions are back to zero and the next call under the chosen
+    configuration still equals the oracle."""
+    gens = _gens([11213, 23209, 521])
+    reqs, total = _blocked([(0, 0, 200000), (1, 2, 150000), (2, 1, 90000)])
+    pool = lib_pool(gens)
+    scratch = torch.zeros(total, dtype=torch.int32, device="cuda")
+    best, ms = pool.autotune(reqs, scratch)
+    assert ms > 0 and best.threads in (32, 64, 128, 256, 512, 1024) and best.pieces in (0, 1)
+    assert [pool.position(g) for g in range(3)] == [0, 0, 0]
+    out = torch.zeros(total, dtype=torch.int32, device="cuda")
+    pool.generate(reqs, out)
+    torch.cuda.synchronize()
+    _check(gens, reqs, as_u32(out), pool)

@@ -52,49 +52,78 @@ __device__ __forceinline__ void round_sync()
         __syncthreads();
 }
 
+// QN slots of a full round, processed stage by stage so that their
+// dependency chains interleave: all shared loads, the recursion up to the
+// table look-up (Sec. 3.6), the look-ups, the tempering (Sec. 3.7), then the
+// stores.  x points at this thread's x_{rS+tid}, out at its output slot.
+// When QN = Q the last slot is the round's tail and only lanes with
+// last_lane set keep its result.
+template <int T, int Q, int QN, int DT>
+__device__ __forceinline__ void round_slots(const GenCtx &g, uint32_t *x, uint32_t (&prev)[Q],
+                                            uint32_t *__restrict__ out, bool last_lane)
+{
+    if constexpr (QN > 0) {
+        const uint32_t *xt_p = x + (g.M - 1u);
+        uint32_t *xn_p = x + g.N;
+        uint32_t a[QN], b[QN], c[QN], u[QN];
+#pragma unroll
+        for (int q = 0; q < QN; ++q) {         // shared loads: x_i, x_{i+1}, x_{M-1+i}
+            a[q] = x[q * T];
+            b[q] = x[q * T + 1];
+            c[q] = xt_p[q * T];
+        }
+#pragma unroll
+        for (int q = 0; q < QN; ++q) {
+            const uint32_t t = b[q] ^ (a[q] & g.mask);
+            u[q] = t ^ (t << g.sh1) ^ (prev[q] >> g.sh2);
+        }
+#pragma unroll
+        for (int q = 0; q < QN; ++q)
+            b[q] = __shfl_sync(0xffffffffu, g.rec_r, (int)u[q], 16);
+#pragma unroll
+        for (int q = 0; q < QN; ++q) {
+            uint32_t s = c[q] ^ (c[q] >> 16);
+            s ^= s >> 8;
+            c[q] = __shfl_sync(0xffffffffu, g.tmp_r, (int)s, 16);
+        }
+#pragma unroll
+        for (int q = 0; q < QN; ++q) {
+            const uint32_t xn = u[q] ^ b[q];
+            if (q + 1 < QN || QN < Q || last_lane) {
+                xn_p[q * T] = xn;
+                prev[q] = xn;
+                __stcs(out + q * T, finish(DT, xn ^ c[q]));
+            }
+        }
+    }
+}
+
 // A full round of S words whose outputs all belong to one blocked segment of
-// dtype DT.  x points at this thread's x_{rS+tid}, out at its output slot.
-// Q = ceil(S / T): slots 0 .. Q-2 are full for every thread; slot Q-1 holds
-// the last S - (Q-1) T columns, and warps with none of them skip it.  The
-// full slots are processed stage by stage so their dependency chains
-// interleave.
-template <int T, int Q, int DT>
+// dtype DT.  Q = ceil(S / T): slots 0 .. Q-2 are full for every thread; slot
+// Q-1 holds the last S - (Q-1) T columns.  Two schedules for the tail slot:
+//   IL (interleaved): warps with tail columns run all Q slots as one chain
+//     of dependent steps -- the shortest round, for launches with fewer work
+//     items than SMs, where each block's round latency is the time;
+//   otherwise (separate): every warp runs Q-1 slots, then warps with tail
+//     columns run the tail slot -- measured faster when many blocks share
+//     each SM.  The two are separate kernels: one kernel with a run-time
+//     choice measured slower than either.
+template <int T, int Q, int DT, bool IL>
 __device__ __forceinline__ void round_fast(const GenCtx &g, uint32_t *x, uint32_t (&prev)[Q],
                                            uint32_t *__restrict__ out, bool tail_warp, bool tail_lane)
 {
-    constexpr int F = Q - 1;                  // full slots
-    const uint32_t *xt_p = x + (g.M - 1u);
-    uint32_t *xn_p = x + g.N;
-    uint32_t a[Q], b[Q], c[Q], u[Q];
-#pragma unroll
-    for (int q = 0; q < F; ++q) {             // shared loads: x_i, x_{i+1}, x_{M-1+i}
-        a[q] = x[q * T];
-        b[q] = x[q * T + 1];
-        c[q] = xt_p[q * T];
+    if constexpr (IL) {
+        if (tail_warp)
+            round_slots<T, Q, Q, DT>(g, x, prev, out, tail_lane);
+        else
+            round_slots<T, Q, Q - 1, DT>(g, x, prev, out, true);
+        return;
     }
-#pragma unroll
-    for (int q = 0; q < F; ++q) {             // recursion up to the table look-up (Sec. 3.6)
-        const uint32_t t = b[q] ^ (a[q] & g.mask);
-        u[q] = t ^ (t << g.sh1) ^ (prev[q] >> g.sh2);
-    }
-#pragma unroll
-    for (int q = 0; q < F; ++q)
-        b[q] = __shfl_sync(0xffffffffu, g.rec_r, (int)u[q], 16);
-#pragma unroll
-    for (int q = 0; q < F; ++q) {             // tempering index from x_{M-1+i} (Sec. 3.7)
-        uint32_t s = c[q] ^ (c[q] >> 16);
-        s ^= s >> 8;
-        c[q] = __shfl_sync(0xffffffffu, g.tmp_r, (int)s, 16);
-    }
-#pragma unroll
-    for (int q = 0; q < F; ++q) {
-        const uint32_t xn = u[q] ^ b[q];
-        xn_p[q * T] = xn;
-        prev[q] = xn;
-        __stcs(out + q * T, finish(DT, xn ^ c[q]));
-    }
+    round_slots<T, Q, Q - 1, DT>(g, x, prev, out, true);
     if (tail_warp) {
-        constexpr int q = F;
+        constexpr int q = Q - 1;
+        const uint32_t *xt_p = x + (g.M - 1u);
+        uint32_t *xn_p = x + g.N;
         const uint32_t a0 = x[q * T], b0 = x[q * T + 1], c0 = xt_p[q * T];
         const uint32_t t = b0 ^ (a0 & g.mask);
         const uint32_t uu = t ^ (t << g.sh1) ^ (prev[q] >> g.sh2);
@@ -111,7 +140,7 @@ __device__ __forceinline__ void round_fast(const GenCtx &g, uint32_t *x, uint32_
 }
 
 // Runs `rounds` full rounds inside one blocked segment of dtype DT.
-template <int T, int Q, int DT>
+template <int T, int Q, int DT, bool IL>
 __device__ __forceinline__ void run_fast(const GenCtx &g, uint32_t *buf, uint32_t B, uint32_t &rel,
                                          uint32_t (&prev)[Q], uint32_t rounds, uint32_t *out)
 {
@@ -125,7 +154,7 @@ __device__ __forceinline__ void run_fast(const GenCtx &g, uint32_t *buf, uint32_
             round_sync<T>();
             rel = 0;
         }
-        round_fast<T, Q, DT>(g, buf + rel + tid, prev, out, tail_warp, tail_lane);
+        round_fast<T, Q, DT, IL>(g, buf + rel + tid, prev, out, tail_warp, tail_lane);
         round_sync<T>();
         rel += g.S;
         out += g.S;
@@ -197,8 +226,9 @@ __device__ __forceinline__ void maybe_compact(const GenCtx &g, uint32_t *buf, ui
 }
 
 // All rounds of one work item (a generator's consecutive segments), with
-// Q = ceil(S / T) column slots per thread.
-template <int T, int Q>
+// Q = ceil(S / T) column slots per thread; IL selects the tail schedule of
+// round_fast.
+template <int T, int Q, bool IL>
 __device__ __forceinline__ void run_item(const GenCtx g, uint32_t *buf, uint32_t B, const DevWork w,
                                       const DevSeg *segs, uint32_t *out_base, uint32_t *st)
 {
@@ -221,11 +251,11 @@ __device__ __forceinline__ void run_item(const GenCtx g, uint32_t *buf, uint32_t
             uint32_t *out = out_base + sg.out_off + (k0 - seg_start);
             const uint32_t rounds = (uint32_t)min(full, (uint64_t)0x7FFFFFFFu);
             if (sg.dtype == 0u)
-                run_fast<T, Q, 0>(g, buf, B, rel, prev, rounds, out);
+                run_fast<T, Q, 0, IL>(g, buf, B, rel, prev, rounds, out);
             else if (sg.dtype == 1u)
-                run_fast<T, Q, 1>(g, buf, B, rel, prev, rounds, out);
+                run_fast<T, Q, 1, IL>(g, buf, B, rel, prev, rounds, out);
             else
-                run_fast<T, Q, 2>(g, buf, B, rel, prev, rounds, out);
+                run_fast<T, Q, 2, IL>(g, buf, B, rel, prev, rounds, out);
             k0 += (uint64_t)rounds * g.S;
         } else {
             maybe_compact<T, Q>(g, buf, B, rel);
@@ -242,17 +272,17 @@ __device__ __forceinline__ void run_item(const GenCtx g, uint32_t *buf, uint32_t
 
 // Runs the work item with the slot count Q = ceil(S / T) it needs, searching
 // the compiled counts QMAX, QMAX-1, ..., 1.  Returns false if none matches.
-template <int T, int QMAX>
+template <int T, int QMAX, bool IL>
 __device__ __forceinline__ bool dispatch_slots(uint32_t nq, const GenCtx &g, uint32_t *buf, uint32_t B,
                                                const DevWork &w, const DevSeg *segs, uint32_t *out,
                                                uint32_t *st)
 {
     if (nq == (uint32_t)QMAX) {
-        run_item<T, QMAX>(g, buf, B, w, segs, out, st);
+        run_item<T, QMAX, IL>(g, buf, B, w, segs, out, st);
         return true;
     }
     if constexpr (QMAX > 1)
-        return dispatch_slots<T, QMAX - 1>(nq, g, buf, B, w, segs, out, st);
+        return dispatch_slots<T, QMAX - 1, IL>(nq, g, buf, B, w, segs, out, st);
     else
         return false;
 }
@@ -560,7 +590,7 @@ __global__ void __launch_bounds__(2 * RT, (2 * RT) >= 512 ? 1 : 512 / (2 * RT)) 
     }
 }
 
-template <int T, int QMAX>
+template <int T, int QMAX, bool IL = false>
 __global__ void __launch_bounds__(T, QMAX <= 6 ? 512 / T : (T >= 256 ? 1 : 256 / T)) k_generate(const LaunchArgs a)
 {
     extern __shared__ __align__(16) uint32_t buf[];
@@ -597,7 +627,7 @@ __global__ void __launch_bounds__(T, QMAX <= 6 ? 512 / T : (T >= 256 ? 1 : 256 /
             if (piece && !(w.flags & kItemLast)) st = nullptr;
             for (uint32_t j = tid; j < g.N; j += T) buf[j] = ld[j];
             __syncthreads();
-            ok = dispatch_slots<T, QMAX>(nq, g, buf, B, w, a.segs + w.seg_begin, out, st);
+            ok = dispatch_slots<T, QMAX, IL>(nq, g, buf, B, w, a.segs + w.seg_begin, out, st);
             if (ok && tid == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&gd.count), (unsigned long long)w.total);
         }
         if (!ok && tid == 0) atomicOr(a.err, kErrBuffer);

@@ -584,10 +584,13 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
         }
     }
     uint32_t grid = (uint32_t)plan.work.size();
+    // fewer work items than SMs: each block's round latency is the time, so
+    // the kernel with interleaved round tails (where compiled)
+    const bool interleave = plan.work.size() < (size_t)std::max(p->sm_count, 1);
     if (c.persistent) {
         CU(cudaMemsetAsync(p->d_ctl, 0, sizeof(unsigned), s), "reset work counter");
         int occ = 0;
-        CU(generate_occupancy(c.threads, c.form, qmax, B, &occ), "occupancy");
+        CU(generate_occupancy(c.threads, c.form, qmax, B, &occ, interleave), "occupancy");
         if (occ < 1) return fail(MTGP_EINVAL, "configuration does not fit on an SM");
         const int per_sm = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, occ) : occ;
         grid = std::min<uint32_t>(grid, (uint32_t)(per_sm * p->sm_count));
@@ -604,6 +607,7 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     a.buf_words = B;
     a.persistent = c.persistent;
     a.jstate = p->d_jstate;
+    a.interleave = interleave ? 1u : 0u;
     CU(launch_generate(a, c.threads, c.form, qmax, grid, s), "generate kernel launch");
     p->launches += 1u;
     CU(cudaEventRecord(p->ev_done, s), "cudaEventRecord");

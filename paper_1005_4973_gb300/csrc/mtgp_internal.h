@@ -64,6 +64,7 @@ struct LaunchArgs {
     uint32_t *const *out_dev;           // shared buffer, >= 2N + S + 32 words for every item
     uint32_t persistent;
     const uint32_t *jstate;             // start states of pieces (DevWork::src)
+    uint32_t interleave;                // 1: interleaved round tails where compiled (latency-bound launches)
 };
 
 // One job of the jump kernels: walk the recursion (Sec. 3.6) from the state at
@@ -108,6 +109,7 @@ typedef void (*GenKernel)(const LaunchArgs);
 GenKernel gen_kernel_t32(uint32_t qmax);
 GenKernel gen_kernel_t64(uint32_t qmax);
 GenKernel gen_kernel_t128(uint32_t qmax);
+GenKernel gen_kernel_t128_il(uint32_t qmax);   // interleaved round tails (LaunchArgs::interleave)
 GenKernel gen_kernel_t256(uint32_t qmax);
 GenKernel gen_kernel_t512(uint32_t qmax);
 // Warp-specialised kernels: blocks of 2 RT threads (RT recursion + RT output).
@@ -133,7 +135,7 @@ cudaError_t launch_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
 cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t form, uint32_t qmax, uint32_t grid,
                             cudaStream_t s);
 cudaError_t generate_occupancy(uint32_t threads, uint32_t form, uint32_t qmax, uint32_t buf_words,
-                               int *blocks_per_sm);
+                               int *blocks_per_sm, bool interleave = false);
 cudaError_t launch_fill(uint32_t *buf, uint64_t words, uint32_t pattern, cudaStream_t s);
 
 }  // namespace mtgp

@@ -51,8 +51,12 @@ __global__ void k_fill(uint4 *buf, uint64_t n16, uint32_t pattern)
     }
 }
 
-GenKernel pick(uint32_t threads, uint32_t form, uint32_t qmax)
+GenKernel pick(uint32_t threads, uint32_t form, uint32_t qmax, bool interleave = false)
 {
+    if (interleave && form == 0u && threads == 128u) {
+        GenKernel k = gen_kernel_t128_il(qmax);
+        if (k) return k;
+    }
     if (form == 2u) {
         switch (threads) {
         case 128: return flow_kernel_w2(qmax);
@@ -110,7 +114,7 @@ cudaError_t launch_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
 cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t form, uint32_t qmax, uint32_t grid,
                             cudaStream_t s)
 {
-    GenKernel k = pick(threads, form, qmax);
+    GenKernel k = pick(threads, form, qmax, a.interleave != 0u);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = (size_t)a.buf_words * sizeof(uint32_t);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -127,9 +131,9 @@ cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t form
 }
 
 cudaError_t generate_occupancy(uint32_t threads, uint32_t form, uint32_t qmax, uint32_t buf_words,
-                               int *blocks_per_sm)
+                               int *blocks_per_sm, bool interleave)
 {
-    GenKernel k = pick(threads, form, qmax);
+    GenKernel k = pick(threads, form, qmax, interleave);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = (size_t)buf_words * sizeof(uint32_t);
     if (smem + 1024u > 48u * 1024u) {     // dynamic + the kernels' static words past the default

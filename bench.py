@@ -426,6 +426,9 @@ def main():
     torch.cuda.synchronize()
     t_host1 = time.perf_counter()
     launches = pool.launch_count() - launches0
+    errs = pool.errors()                                 # shape / bounded-wait flags of the timed launches
+    if errs:
+        raise SystemExit(f"bench: kernel error flags {errs:#x} set during the timed steps; outputs invalid")
     if dist:
         dist.barrier()
     ms_total = e0.elapsed_time(e1)

@@ -224,6 +224,20 @@ mtgp_status check_config(const mtgp_config &c)
     return MTGP_OK;
 }
 
+// Entry points that allocate host memory (containers) return MTGP_ENOMEM
+// instead of letting an exception cross the C ABI.
+template <class F>
+mtgp_status guarded(F &&f)
+{
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        return fail(MTGP_ENOMEM, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(MTGP_EINVAL, "%s", e.what());
+    }
+}
+
 // Waits until the pool's last work finished (for synchronous calls).
 mtgp_status pool_sync(mtgp_pool *p)
 {
@@ -694,79 +708,86 @@ mtgp_status mtgp_params_validate(const mtgp_params *p)
 mtgp_status mtgp_pool_create(const mtgp_params *ps, const uint32_t *gen_ids, const uint64_t *seeds,
                              uint32_t count, void *stream, mtgp_pool **out)
 {
-    if (!out) return fail(MTGP_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (!ps || !gen_ids || !seeds || count == 0) return fail(MTGP_EINVAL, "empty or NULL pool arguments");
-    for (uint32_t i = 0; i < count; ++i) {
-        mtgp_status st = mtgp_params_validate(&ps[i]);
-        if (st != MTGP_OK) {
-            std::string m = g_err;
-            return fail(st, "parameter set %u: %s", i, m.c_str());
+    return guarded([&]() -> mtgp_status {
+        if (!out) return fail(MTGP_EINVAL, "out is NULL");
+        *out = nullptr;
+        if (!ps || !gen_ids || !seeds || count == 0) return fail(MTGP_EINVAL, "empty or NULL pool arguments");
+        for (uint32_t i = 0; i < count; ++i) {
+            mtgp_status st = mtgp_params_validate(&ps[i]);
+            if (st != MTGP_OK) {
+                std::string m = g_err;
+                return fail(st, "parameter set %u: %s", i, m.c_str());
+            }
         }
-    }
-    cudaStream_t s = (cudaStream_t)stream;
-    mtgp_pool *p = new (std::nothrow) mtgp_pool;
-    if (!p) return fail(MTGP_ENOMEM, "host allocation");
-    p->count = count;
-    p->cfg = kDefaultConfig;
-    p->host_gens.resize(count);
-    p->jc.ann.resize(count);
-    uint64_t off = 0;
-    for (uint32_t i = 0; i < count; ++i) {
-        DevGen &g = p->host_gens[i];
-        std::memset(&g, 0, sizeof g);
-        g.N = ps[i].N;
-        g.M = ps[i].pos;
-        g.mask = ps[i].mask;
-        g.sh1 = ps[i].sh1;
-        g.sh2 = ps[i].sh2;
-        g.mexp = ps[i].mexp;
-        g.id = ps[i].id;
-        g.state_off = off;
-        std::memcpy(g.rec, ps[i].rec_tbl, sizeof g.rec);
-        std::memcpy(g.tmp, ps[i].tmp_tbl, sizeof g.tmp);
-        off += (g.N + 3u) & ~3u;                   // 16-byte aligned states
-        p->max_N = std::max(p->max_N, g.N);
-    }
-    p->state_words = off;
-    auto cleanup = [&](mtgp_status st) { mtgp_pool_destroy(p); return st; };
-    cudaError_t e;
-#define CUP(call, what)                                           \
-    do {                                                          \
-        e = (call);                                               \
-        if (e != cudaSuccess) return cleanup(cuda_fail(e, what)); \
-    } while (0)
-    CUP(cudaGetDevice(&p->device), "cudaGetDevice");
-    CUP(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device), "SM count");
-    CUP(cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming), "cudaEventCreate");
-    CUP(cudaEventCreateWithFlags(&p->ev_upload, cudaEventDisableTiming), "cudaEventCreate");
-    CUP(cudaMalloc(&p->d_gens, sizeof(DevGen) * count), "cudaMalloc generators");
-    CUP(cudaMalloc(&p->d_state, sizeof(uint32_t) * off), "cudaMalloc states");
-    CUP(cudaMalloc(&p->d_ctl, 4 * sizeof(unsigned)), "cudaMalloc control");
-    CUP(cudaMemsetAsync(p->d_ctl, 0, 4 * sizeof(unsigned), s), "cudaMemsetAsync");
-    // upload parameters and seeding inputs through one pinned staging buffer
-    const size_t gbytes = sizeof(DevGen) * count, ibytes = sizeof(uint32_t) * count,
-                 sbytes = sizeof(uint64_t) * count;
-    const size_t ioff = gbytes, soff = (gbytes + ibytes + 15u) & ~(size_t)15u;
-    mtgp_status st = ensure_upload_space(p, soff + sbytes);
-    if (st != MTGP_OK) return cleanup(st);
-    std::memcpy(p->h_stage, p->host_gens.data(), gbytes);
-    std::memcpy((char *)p->h_stage + ioff, gen_ids, ibytes);
-    std::memcpy((char *)p->h_stage + soff, seeds, sbytes);
-    CUP(cudaMemcpyAsync(p->d_gens, p->h_stage, gbytes, cudaMemcpyHostToDevice, s), "upload generators");
-    CUP(cudaMemcpyAsync(p->d_work, (char *)p->h_stage + ioff, soff + sbytes - ioff, cudaMemcpyHostToDevice, s),
-        "upload seeds");
-    CUP(launch_seed(p->d_gens, p->d_state, (const uint32_t *)p->d_work,
-                    (const uint64_t *)((char *)p->d_work + (soff - ioff)), 0, count, s),
-        "seed kernel launch");
-    CUP(cudaEventRecord(p->ev_upload, s), "cudaEventRecord");
-    p->upload_pending = true;
-    CUP(cudaEventRecord(p->ev_done, s), "cudaEventRecord");
-    p->last_stream = s;
-    p->used = true;
-#undef CUP
-    *out = p;
-    return MTGP_OK;
+        cudaStream_t s = (cudaStream_t)stream;
+        mtgp_pool *p = new (std::nothrow) mtgp_pool;
+        if (!p) return fail(MTGP_ENOMEM, "host allocation");
+        p->count = count;
+        p->cfg = kDefaultConfig;
+        try {
+            p->host_gens.resize(count);
+            p->jc.ann.resize(count);
+        } catch (const std::exception &) {
+            delete p;
+            return fail(MTGP_ENOMEM, "host allocation");
+        }
+        uint64_t off = 0;
+        for (uint32_t i = 0; i < count; ++i) {
+            DevGen &g = p->host_gens[i];
+            std::memset(&g, 0, sizeof g);
+            g.N = ps[i].N;
+            g.M = ps[i].pos;
+            g.mask = ps[i].mask;
+            g.sh1 = ps[i].sh1;
+            g.sh2 = ps[i].sh2;
+            g.mexp = ps[i].mexp;
+            g.id = ps[i].id;
+            g.state_off = off;
+            std::memcpy(g.rec, ps[i].rec_tbl, sizeof g.rec);
+            std::memcpy(g.tmp, ps[i].tmp_tbl, sizeof g.tmp);
+            off += (g.N + 3u) & ~3u;                   // 16-byte aligned states
+            p->max_N = std::max(p->max_N, g.N);
+        }
+        p->state_words = off;
+        auto cleanup = [&](mtgp_status st) { mtgp_pool_destroy(p); return st; };
+        cudaError_t e;
+    #define CUP(call, what)                                           \
+        do {                                                          \
+            e = (call);                                               \
+            if (e != cudaSuccess) return cleanup(cuda_fail(e, what)); \
+        } while (0)
+        CUP(cudaGetDevice(&p->device), "cudaGetDevice");
+        CUP(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device), "SM count");
+        CUP(cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming), "cudaEventCreate");
+        CUP(cudaEventCreateWithFlags(&p->ev_upload, cudaEventDisableTiming), "cudaEventCreate");
+        CUP(cudaMalloc(&p->d_gens, sizeof(DevGen) * count), "cudaMalloc generators");
+        CUP(cudaMalloc(&p->d_state, sizeof(uint32_t) * off), "cudaMalloc states");
+        CUP(cudaMalloc(&p->d_ctl, 4 * sizeof(unsigned)), "cudaMalloc control");
+        CUP(cudaMemsetAsync(p->d_ctl, 0, 4 * sizeof(unsigned), s), "cudaMemsetAsync");
+        // upload parameters and seeding inputs through one pinned staging buffer
+        const size_t gbytes = sizeof(DevGen) * count, ibytes = sizeof(uint32_t) * count,
+                     sbytes = sizeof(uint64_t) * count;
+        const size_t ioff = gbytes, soff = (gbytes + ibytes + 15u) & ~(size_t)15u;
+        mtgp_status st = ensure_upload_space(p, soff + sbytes);
+        if (st != MTGP_OK) return cleanup(st);
+        std::memcpy(p->h_stage, p->host_gens.data(), gbytes);
+        std::memcpy((char *)p->h_stage + ioff, gen_ids, ibytes);
+        std::memcpy((char *)p->h_stage + soff, seeds, sbytes);
+        CUP(cudaMemcpyAsync(p->d_gens, p->h_stage, gbytes, cudaMemcpyHostToDevice, s), "upload generators");
+        CUP(cudaMemcpyAsync(p->d_work, (char *)p->h_stage + ioff, soff + sbytes - ioff, cudaMemcpyHostToDevice, s),
+            "upload seeds");
+        CUP(launch_seed(p->d_gens, p->d_state, (const uint32_t *)p->d_work,
+                        (const uint64_t *)((char *)p->d_work + (soff - ioff)), 0, count, s),
+            "seed kernel launch");
+        CUP(cudaEventRecord(p->ev_upload, s), "cudaEventRecord");
+        p->upload_pending = true;
+        CUP(cudaEventRecord(p->ev_done, s), "cudaEventRecord");
+        p->last_stream = s;
+        p->used = true;
+    #undef CUP
+        *out = p;
+        return MTGP_OK;
+    });
 }
 
 mtgp_status mtgp_pool_info(const mtgp_pool *p, uint32_t *count, uint64_t *device_bytes)
@@ -798,97 +819,101 @@ mtgp_status mtgp_pool_set_config(mtgp_pool *p, const mtgp_config *cfg)
 mtgp_status mtgp_pool_generate(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_out,
                                mtgp_layout layout, void *stream)
 {
-    if (!p) return fail(MTGP_EINVAL, "pool is NULL");
-    return pool_run(p, reqs, nreq, dev_out, layout, (cudaStream_t)stream);
+    return guarded([&]() -> mtgp_status {
+        if (!p) return fail(MTGP_EINVAL, "pool is NULL");
+        return pool_run(p, reqs, nreq, dev_out, layout, (cudaStream_t)stream);
+    });
 }
 
 mtgp_status mtgp_pool_generate_host(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *host_out,
                                     mtgp_layout layout, uint64_t staging_bytes, void *stream)
 {
-    if (!p) return fail(MTGP_EINVAL, "pool is NULL");
-    if (layout != MTGP_LAYOUT_BLOCKED) return fail(MTGP_EINVAL, "host output supports the blocked layout only");
-    if (nreq && !reqs) return fail(MTGP_EINVAL, "reqs is NULL");
-    cudaStream_t s = (cudaStream_t)stream;
-    mtgp_status st = pool_busy_check(p, s);
-    if (st != MTGP_OK) return st;
-    uint64_t total = 0;
-    for (uint32_t j = 0; j < nreq; ++j) {
-        if (reqs[j].gen >= p->count || reqs[j].dtype > 2u) return fail(MTGP_EINVAL, "request %u invalid", j);
-        total += reqs[j].n;
-    }
-    if (!total) return MTGP_OK;
-    if (!host_out) return fail(MTGP_EINVAL, "host_out is NULL");
-    if (!staging_bytes) staging_bytes = 1ull << 30;
-    staging_bytes &= ~15ull;
-    if (staging_bytes < 4096u) return fail(MTGP_EINVAL, "staging_bytes too small");
-    if (staging_bytes > p->e2e_bytes) {
-        st = pool_sync(p);
+    return guarded([&]() -> mtgp_status {
+        if (!p) return fail(MTGP_EINVAL, "pool is NULL");
+        if (layout != MTGP_LAYOUT_BLOCKED) return fail(MTGP_EINVAL, "host output supports the blocked layout only");
+        if (nreq && !reqs) return fail(MTGP_EINVAL, "reqs is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        mtgp_status st = pool_busy_check(p, s);
         if (st != MTGP_OK) return st;
-        for (int b = 0; b < 2; ++b) {
-            if (p->d_e2e[b]) CU(cudaFree(p->d_e2e[b]), "cudaFree");
-            p->d_e2e[b] = nullptr;
+        uint64_t total = 0;
+        for (uint32_t j = 0; j < nreq; ++j) {
+            if (reqs[j].gen >= p->count || reqs[j].dtype > 2u) return fail(MTGP_EINVAL, "request %u invalid", j);
+            total += reqs[j].n;
         }
-        p->e2e_bytes = 0;
-        for (int b = 0; b < 2; ++b) CU(cudaMalloc(&p->d_e2e[b], staging_bytes), "cudaMalloc staging");
-        p->e2e_bytes = staging_bytes;
-    }
-    if (!p->copy_stream) {
-        CU(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
-        for (int b = 0; b < 2; ++b) {
-            CU(cudaEventCreateWithFlags(&p->ev_gen[b], cudaEventDisableTiming), "cudaEventCreate");
-            CU(cudaEventCreateWithFlags(&p->ev_copy[b], cudaEventDisableTiming), "cudaEventCreate");
-            CU(cudaEventRecord(p->ev_copy[b], p->copy_stream), "cudaEventRecord");
-        }
-    }
-    const uint64_t cap = p->e2e_bytes / 4u;
-    std::vector<Slice> slices;
-    std::vector<mtgp_request> batch;
-    int buf = 0;
-    auto flush = [&]() -> mtgp_status {
-        if (slices.empty()) return MTGP_OK;
-        CU(cudaStreamWaitEvent(s, p->ev_copy[buf], 0), "cudaStreamWaitEvent");
-        batch.clear();
-        uint64_t off = 0;
-        for (const Slice &sl : slices) {
-            batch.push_back(mtgp_request{sl.gen, sl.dtype, sl.n, off});
-            off += sl.n;
-        }
-        mtgp_status r = pool_run(p, batch.data(), (uint32_t)batch.size(), p->d_e2e[buf], MTGP_LAYOUT_BLOCKED, s);
-        if (r != MTGP_OK) return r;
-        CU(cudaEventRecord(p->ev_gen[buf], s), "cudaEventRecord");
-        CU(cudaStreamWaitEvent(p->copy_stream, p->ev_gen[buf], 0), "cudaStreamWaitEvent");
-        off = 0;
-        for (const Slice &sl : slices) {
-            CU(cudaMemcpyAsync((char *)host_out + 4u * sl.host_off, (char *)p->d_e2e[buf] + 4u * off, 4u * sl.n,
-                               cudaMemcpyDeviceToHost, p->copy_stream),
-               "copy to host");
-            off += sl.n;
-        }
-        CU(cudaEventRecord(p->ev_copy[buf], p->copy_stream), "cudaEventRecord");
-        slices.clear();
-        buf ^= 1;
-        return MTGP_OK;
-    };
-    uint64_t used = 0;
-    for (uint32_t j = 0; j < nreq; ++j) {
-        uint64_t left = reqs[j].n, host_off = reqs[j].out_offset;
-        while (left) {
-            if (used == cap) {
-                st = flush();
-                if (st != MTGP_OK) return st;
-                used = 0;
+        if (!total) return MTGP_OK;
+        if (!host_out) return fail(MTGP_EINVAL, "host_out is NULL");
+        if (!staging_bytes) staging_bytes = 1ull << 30;
+        staging_bytes &= ~15ull;
+        if (staging_bytes < 4096u) return fail(MTGP_EINVAL, "staging_bytes too small");
+        if (staging_bytes > p->e2e_bytes) {
+            st = pool_sync(p);
+            if (st != MTGP_OK) return st;
+            for (int b = 0; b < 2; ++b) {
+                if (p->d_e2e[b]) CU(cudaFree(p->d_e2e[b]), "cudaFree");
+                p->d_e2e[b] = nullptr;
             }
-            const uint64_t take = std::min(left, cap - used);
-            slices.push_back(Slice{reqs[j].gen, reqs[j].dtype, take, host_off});
-            used += take;
-            left -= take;
-            host_off += take;
+            p->e2e_bytes = 0;
+            for (int b = 0; b < 2; ++b) CU(cudaMalloc(&p->d_e2e[b], staging_bytes), "cudaMalloc staging");
+            p->e2e_bytes = staging_bytes;
         }
-    }
-    st = flush();
-    if (st != MTGP_OK) return st;
-    CU(cudaStreamSynchronize(p->copy_stream), "cudaStreamSynchronize");
-    return MTGP_OK;
+        if (!p->copy_stream) {
+            CU(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+            for (int b = 0; b < 2; ++b) {
+                CU(cudaEventCreateWithFlags(&p->ev_gen[b], cudaEventDisableTiming), "cudaEventCreate");
+                CU(cudaEventCreateWithFlags(&p->ev_copy[b], cudaEventDisableTiming), "cudaEventCreate");
+                CU(cudaEventRecord(p->ev_copy[b], p->copy_stream), "cudaEventRecord");
+            }
+        }
+        const uint64_t cap = p->e2e_bytes / 4u;
+        std::vector<Slice> slices;
+        std::vector<mtgp_request> batch;
+        int buf = 0;
+        auto flush = [&]() -> mtgp_status {
+            if (slices.empty()) return MTGP_OK;
+            CU(cudaStreamWaitEvent(s, p->ev_copy[buf], 0), "cudaStreamWaitEvent");
+            batch.clear();
+            uint64_t off = 0;
+            for (const Slice &sl : slices) {
+                batch.push_back(mtgp_request{sl.gen, sl.dtype, sl.n, off});
+                off += sl.n;
+            }
+            mtgp_status r = pool_run(p, batch.data(), (uint32_t)batch.size(), p->d_e2e[buf], MTGP_LAYOUT_BLOCKED, s);
+            if (r != MTGP_OK) return r;
+            CU(cudaEventRecord(p->ev_gen[buf], s), "cudaEventRecord");
+            CU(cudaStreamWaitEvent(p->copy_stream, p->ev_gen[buf], 0), "cudaStreamWaitEvent");
+            off = 0;
+            for (const Slice &sl : slices) {
+                CU(cudaMemcpyAsync((char *)host_out + 4u * sl.host_off, (char *)p->d_e2e[buf] + 4u * off, 4u * sl.n,
+                                   cudaMemcpyDeviceToHost, p->copy_stream),
+                   "copy to host");
+                off += sl.n;
+            }
+            CU(cudaEventRecord(p->ev_copy[buf], p->copy_stream), "cudaEventRecord");
+            slices.clear();
+            buf ^= 1;
+            return MTGP_OK;
+        };
+        uint64_t used = 0;
+        for (uint32_t j = 0; j < nreq; ++j) {
+            uint64_t left = reqs[j].n, host_off = reqs[j].out_offset;
+            while (left) {
+                if (used == cap) {
+                    st = flush();
+                    if (st != MTGP_OK) return st;
+                    used = 0;
+                }
+                const uint64_t take = std::min(left, cap - used);
+                slices.push_back(Slice{reqs[j].gen, reqs[j].dtype, take, host_off});
+                used += take;
+                left -= take;
+                host_off += take;
+            }
+        }
+        st = flush();
+        if (st != MTGP_OK) return st;
+        CU(cudaStreamSynchronize(p->copy_stream), "cudaStreamSynchronize");
+        return MTGP_OK;
+    });
 }
 
 mtgp_status mtgp_pool_position(mtgp_pool *p, uint32_t i, uint64_t *pos)
@@ -938,29 +963,31 @@ mtgp_status mtgp_pool_save(mtgp_pool *p, void *host_buf, size_t *bytes)
 
 mtgp_status mtgp_pool_load(mtgp_pool *p, const void *host_buf, size_t bytes)
 {
-    if (!p || !host_buf) return fail(MTGP_EINVAL, "NULL argument");
-    const size_t need = 16u + sizeof(DevGen) * p->count + 4u * p->state_words;
-    if (bytes != need) return fail(MTGP_EINVAL, "checkpoint of %zu bytes, expected %zu", bytes, need);
-    uint32_t hdr[4];
-    std::memcpy(hdr, host_buf, 16);
-    if (hdr[0] != 0x5047544Du || hdr[1] != MTGP_PARAMS_VERSION || hdr[2] != p->count ||
-        hdr[3] != (uint32_t)p->state_words)
-        return fail(MTGP_EINVAL, "checkpoint header does not match this pool");
-    const DevGen *gs = (const DevGen *)((const char *)host_buf + 16);
-    for (uint32_t i = 0; i < p->count; ++i) {
-        DevGen a = gs[i], b = p->host_gens[i];
-        a.count = b.count = 0;
-        if (std::memcmp(&a, &b, sizeof a) != 0)
-            return fail(MTGP_EINVAL, "checkpoint generator %u has other parameters", i);
-    }
-    mtgp_status st = pool_sync(p);
-    if (st != MTGP_OK) return st;
-    CU(cudaMemcpy(p->d_gens, gs, sizeof(DevGen) * p->count, cudaMemcpyHostToDevice), "load generators");
-    CU(cudaMemcpy(p->d_state, (const char *)host_buf + 16 + sizeof(DevGen) * p->count, 4u * p->state_words,
-                  cudaMemcpyHostToDevice),
-       "load states");
-    jump_clear(p->jc, true);   // annihilators belong to the replaced states
-    return MTGP_OK;
+    return guarded([&]() -> mtgp_status {
+        if (!p || !host_buf) return fail(MTGP_EINVAL, "NULL argument");
+        const size_t need = 16u + sizeof(DevGen) * p->count + 4u * p->state_words;
+        if (bytes != need) return fail(MTGP_EINVAL, "checkpoint of %zu bytes, expected %zu", bytes, need);
+        uint32_t hdr[4];
+        std::memcpy(hdr, host_buf, 16);
+        if (hdr[0] != 0x5047544Du || hdr[1] != MTGP_PARAMS_VERSION || hdr[2] != p->count ||
+            hdr[3] != (uint32_t)p->state_words)
+            return fail(MTGP_EINVAL, "checkpoint header does not match this pool");
+        const DevGen *gs = (const DevGen *)((const char *)host_buf + 16);
+        for (uint32_t i = 0; i < p->count; ++i) {
+            DevGen a = gs[i], b = p->host_gens[i];
+            a.count = b.count = 0;
+            if (std::memcmp(&a, &b, sizeof a) != 0)
+                return fail(MTGP_EINVAL, "checkpoint generator %u has other parameters", i);
+        }
+        mtgp_status st = pool_sync(p);
+        if (st != MTGP_OK) return st;
+        CU(cudaMemcpy(p->d_gens, gs, sizeof(DevGen) * p->count, cudaMemcpyHostToDevice), "load generators");
+        CU(cudaMemcpy(p->d_state, (const char *)host_buf + 16 + sizeof(DevGen) * p->count, 4u * p->state_words,
+                      cudaMemcpyHostToDevice),
+           "load states");
+        jump_clear(p->jc, true);   // annihilators belong to the replaced states
+        return MTGP_OK;
+    });
 }
 
 void mtgp_pool_destroy(mtgp_pool *p)
@@ -992,17 +1019,19 @@ void mtgp_pool_destroy(mtgp_pool *p)
 mtgp_status mtgp_state_create(const mtgp_params *params, uint32_t gen_id, uint64_t seed, void *stream,
                               mtgp_state **out)
 {
-    if (!out) return fail(MTGP_EINVAL, "out is NULL");
-    *out = nullptr;
-    mtgp_state *s = new (std::nothrow) mtgp_state;
-    if (!s) return fail(MTGP_ENOMEM, "host allocation");
-    mtgp_status st = mtgp_pool_create(params, &gen_id, &seed, 1u, stream, &s->pool);
-    if (st != MTGP_OK) {
-        delete s;
-        return st;
-    }
-    *out = s;
-    return MTGP_OK;
+    return guarded([&]() -> mtgp_status {
+        if (!out) return fail(MTGP_EINVAL, "out is NULL");
+        *out = nullptr;
+        mtgp_state *s = new (std::nothrow) mtgp_state;
+        if (!s) return fail(MTGP_ENOMEM, "host allocation");
+        mtgp_status st = mtgp_pool_create(params, &gen_id, &seed, 1u, stream, &s->pool);
+        if (st != MTGP_OK) {
+            delete s;
+            return st;
+        }
+        *out = s;
+        return MTGP_OK;
+    });
 }
 
 mtgp_status mtgp_generate(mtgp_state *s, mtgp_dtype dt, void *dev_out, uint64_t n, void *stream)
@@ -1050,171 +1079,177 @@ mtgp_status mtgp_fill_probe(void *dev_buf, uint64_t words, uint32_t pattern, voi
 mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_scratch, void *stream,
                           mtgp_config *best, float *best_ms)
 {
-    if (!p) return fail(MTGP_EINVAL, "pool is NULL");
-    cudaStream_t s = (cudaStream_t)stream;
-    mtgp_status st = pool_busy_check(p, s);
-    if (st != MTGP_OK) return st;
-    size_t bytes = 0;
-    st = mtgp_pool_save(p, nullptr, &bytes);
-    if (st != MTGP_OK) return st;
-    std::vector<char> ckpt(bytes);
-    st = mtgp_pool_save(p, ckpt.data(), &bytes);
-    if (st != MTGP_OK) return st;
-    const mtgp_config orig = p->cfg;
-    std::vector<mtgp_config> cands;
-    for (uint32_t pieces : {0u, 1u})                     // jump-ahead pieces: auto, or none
-        for (uint32_t form : {0u, 1u, 2u})
-            for (uint32_t threads : {32u, 64u, 128u, 256u, 512u, 1024u})
-                for (uint32_t pers : {0u, 1u})
-                    for (uint32_t bps : {0u, 1u, 2u, 3u, 4u, 6u, 8u}) {
-                        if (!pers && bps) continue;
-                        if (!threads_supported(threads, form)) continue;
-                        cands.push_back(mtgp_config{threads, pers, bps, orig.chunk, 0u, form, pieces, 0u});
-                    }
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0), "cudaEventCreate");
-    CU(cudaEventCreate(&e1), "cudaEventCreate");
-    float best_t = 1e30f;
-    mtgp_config best_c = orig;
-    for (const mtgp_config &c : cands) {
-        p->cfg = c;
-        mtgp_status r = pool_run(p, reqs, nreq, dev_scratch, MTGP_LAYOUT_BLOCKED, s);   // warm-up
-        if (r != MTGP_OK) continue;
-        CU(cudaEventRecord(e0, s), "cudaEventRecord");
-        r = pool_run(p, reqs, nreq, dev_scratch, MTGP_LAYOUT_BLOCKED, s);
-        CU(cudaEventRecord(e1, s), "cudaEventRecord");
-        CU(cudaEventSynchronize(e1), "cudaEventSynchronize");
-        float ms = 0.f;
-        CU(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
-        if (r == MTGP_OK && ms < best_t) {
-            best_t = ms;
-            best_c = c;
+    return guarded([&]() -> mtgp_status {
+        if (!p) return fail(MTGP_EINVAL, "pool is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        mtgp_status st = pool_busy_check(p, s);
+        if (st != MTGP_OK) return st;
+        size_t bytes = 0;
+        st = mtgp_pool_save(p, nullptr, &bytes);
+        if (st != MTGP_OK) return st;
+        std::vector<char> ckpt(bytes);
+        st = mtgp_pool_save(p, ckpt.data(), &bytes);
+        if (st != MTGP_OK) return st;
+        const mtgp_config orig = p->cfg;
+        std::vector<mtgp_config> cands;
+        for (uint32_t pieces : {0u, 1u})                     // jump-ahead pieces: auto, or none
+            for (uint32_t form : {0u, 1u, 2u})
+                for (uint32_t threads : {32u, 64u, 128u, 256u, 512u, 1024u})
+                    for (uint32_t pers : {0u, 1u})
+                        for (uint32_t bps : {0u, 1u, 2u, 3u, 4u, 6u, 8u}) {
+                            if (!pers && bps) continue;
+                            if (!threads_supported(threads, form)) continue;
+                            cands.push_back(mtgp_config{threads, pers, bps, orig.chunk, 0u, form, pieces, 0u});
+                        }
+        cudaEvent_t e0, e1;
+        CU(cudaEventCreate(&e0), "cudaEventCreate");
+        CU(cudaEventCreate(&e1), "cudaEventCreate");
+        float best_t = 1e30f;
+        mtgp_config best_c = orig;
+        for (const mtgp_config &c : cands) {
+            p->cfg = c;
+            mtgp_status r = pool_run(p, reqs, nreq, dev_scratch, MTGP_LAYOUT_BLOCKED, s);   // warm-up
+            if (r != MTGP_OK) continue;
+            CU(cudaEventRecord(e0, s), "cudaEventRecord");
+            r = pool_run(p, reqs, nreq, dev_scratch, MTGP_LAYOUT_BLOCKED, s);
+            CU(cudaEventRecord(e1, s), "cudaEventRecord");
+            CU(cudaEventSynchronize(e1), "cudaEventSynchronize");
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            if (r == MTGP_OK && ms < best_t) {
+                best_t = ms;
+                best_c = c;
+            }
         }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    p->cfg = best_c;
-    // psi found while tuning annihilates the restored (earlier) states as well:
-    // psi(F) F^k s = 0 and F is invertible (R4 + I invertible, Sec. 5)
-    const std::vector<f2::Poly> ann = p->jc.ann;
-    st = mtgp_pool_load(p, ckpt.data(), bytes);
-    if (st != MTGP_OK) return st;
-    p->jc.ann = ann;
-    if (best) *best = best_c;
-    if (best_ms) *best_ms = best_t;
-    return MTGP_OK;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        p->cfg = best_c;
+        // psi found while tuning annihilates the restored (earlier) states as well:
+        // psi(F) F^k s = 0 and F is invertible (R4 + I invertible, Sec. 5)
+        const std::vector<f2::Poly> ann = p->jc.ann;
+        st = mtgp_pool_load(p, ckpt.data(), bytes);
+        if (st != MTGP_OK) return st;
+        p->jc.ann = ann;
+        if (best) *best = best_c;
+        if (best_ms) *best_ms = best_t;
+        return MTGP_OK;
+    });
 }
 
 // ---- graph-captured batched launch -------------------------------------------
 mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mtgp_graph **out)
 {
-    if (!p || !out || max_items == 0) return fail(MTGP_EINVAL, "graph: NULL pool/out or max_items == 0");
-    *out = nullptr;
-    cudaStream_t s = (cudaStream_t)stream;
-    mtgp_status st = pool_sync(p);
-    if (st != MTGP_OK) return st;
-    mtgp_config c = p->cfg;
-    c.persistent = 1u;                                   // a fixed grid pulls however many items there are
-    std::vector<uint32_t> all(p->count);
-    for (uint32_t i = 0; i < p->count; ++i) all[i] = i;  // any generator of the pool may appear
-    uint32_t qmax = 0, B = 0;
-    st = launch_shape(p, c, all.data(), all.size(), max_items, &qmax, &B);
-    if (st != MTGP_OK) return st;
-    int occ = 0;
-    CU(generate_occupancy(c.threads, c.form, qmax, B, &occ), "occupancy");
-    if (occ < 1) return fail(MTGP_EINVAL, "graph: configuration does not fit on an SM");
-    const int per_sm = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, occ) : occ;
-    const uint32_t grid = std::min<uint32_t>(max_items, (uint32_t)(per_sm * p->sm_count));
-    mtgp_graph *g = new (std::nothrow) mtgp_graph;
-    if (!g) return fail(MTGP_ENOMEM, "host allocation");
-    g->pool = p;
-    g->max_items = max_items;
-    g->B = B;
-    g->d_bytes = 256u + (size_t)max_items * (sizeof(DevWork) + sizeof(DevSeg));
-    auto bail = [&](mtgp_status r) { mtgp_graph_destroy(g); return r; };
-    cudaError_t e;
-#define CUG(call, what)                                       \
-    do {                                                      \
-        e = (call);                                           \
-        if (e != cudaSuccess) return bail(cuda_fail(e, what)); \
-    } while (0)
-    CUG(cudaMalloc(&g->d_buf, g->d_bytes), "cudaMalloc graph work list");
-    CUG(cudaMemsetAsync(g->d_buf, 0, 256u, s), "cudaMemsetAsync");
-    for (int k = 0; k < 2; ++k) {
-        CUG(cudaHostAlloc(&g->h_stage[k], g->d_bytes, cudaHostAllocDefault), "cudaHostAlloc");
-        CUG(cudaEventCreateWithFlags(&g->ev_stage[k], cudaEventDisableTiming), "cudaEventCreate");
-    }
-    CUG(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-    CUG(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
-    char *b = (char *)g->d_buf;
-    LaunchArgs a{};
-    a.gens = p->d_gens;
-    a.state = p->d_state;
-    a.work = (const DevWork *)(b + 256u);
-    a.segs = (const DevSeg *)(b + 256u + (size_t)max_items * sizeof(DevWork));
-    a.out = nullptr;
-    a.counter = (unsigned *)b;
-    a.err = (unsigned *)(b + 4u);
-    a.nwork = 0;
-    a.nwork_dev = (const uint32_t *)(b + 8u);
-    a.out_dev = (uint32_t *const *)(b + 16u);
-    a.buf_words = B;
-    a.persistent = 1u;
-    CUG(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-    cudaError_t e1 = cudaMemsetAsync(b, 0, sizeof(unsigned), g->cap_stream);
-    cudaError_t e2 = e1 == cudaSuccess ? launch_generate(a, c.threads, c.form, qmax, grid, g->cap_stream) : e1;
-    e = cudaStreamEndCapture(g->cap_stream, &g->graph);
-    if (e2 != cudaSuccess) return bail(cuda_fail(e2, "graph: capture of the generation launch"));
-    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamEndCapture"));
-    CUG(cudaGraphInstantiate(&g->exec, g->graph, 0), "cudaGraphInstantiate");
-#undef CUG
-    *out = g;
-    return MTGP_OK;
+    return guarded([&]() -> mtgp_status {
+        if (!p || !out || max_items == 0) return fail(MTGP_EINVAL, "graph: NULL pool/out or max_items == 0");
+        *out = nullptr;
+        cudaStream_t s = (cudaStream_t)stream;
+        mtgp_status st = pool_sync(p);
+        if (st != MTGP_OK) return st;
+        mtgp_config c = p->cfg;
+        c.persistent = 1u;                                   // a fixed grid pulls however many items there are
+        std::vector<uint32_t> all(p->count);
+        for (uint32_t i = 0; i < p->count; ++i) all[i] = i;  // any generator of the pool may appear
+        uint32_t qmax = 0, B = 0;
+        st = launch_shape(p, c, all.data(), all.size(), max_items, &qmax, &B);
+        if (st != MTGP_OK) return st;
+        int occ = 0;
+        CU(generate_occupancy(c.threads, c.form, qmax, B, &occ), "occupancy");
+        if (occ < 1) return fail(MTGP_EINVAL, "graph: configuration does not fit on an SM");
+        const int per_sm = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, occ) : occ;
+        const uint32_t grid = std::min<uint32_t>(max_items, (uint32_t)(per_sm * p->sm_count));
+        mtgp_graph *g = new (std::nothrow) mtgp_graph;
+        if (!g) return fail(MTGP_ENOMEM, "host allocation");
+        g->pool = p;
+        g->max_items = max_items;
+        g->B = B;
+        g->d_bytes = 256u + (size_t)max_items * (sizeof(DevWork) + sizeof(DevSeg));
+        auto bail = [&](mtgp_status r) { mtgp_graph_destroy(g); return r; };
+        cudaError_t e;
+    #define CUG(call, what)                                       \
+        do {                                                      \
+            e = (call);                                           \
+            if (e != cudaSuccess) return bail(cuda_fail(e, what)); \
+        } while (0)
+        CUG(cudaMalloc(&g->d_buf, g->d_bytes), "cudaMalloc graph work list");
+        CUG(cudaMemsetAsync(g->d_buf, 0, 256u, s), "cudaMemsetAsync");
+        for (int k = 0; k < 2; ++k) {
+            CUG(cudaHostAlloc(&g->h_stage[k], g->d_bytes, cudaHostAllocDefault), "cudaHostAlloc");
+            CUG(cudaEventCreateWithFlags(&g->ev_stage[k], cudaEventDisableTiming), "cudaEventCreate");
+        }
+        CUG(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        CUG(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        char *b = (char *)g->d_buf;
+        LaunchArgs a{};
+        a.gens = p->d_gens;
+        a.state = p->d_state;
+        a.work = (const DevWork *)(b + 256u);
+        a.segs = (const DevSeg *)(b + 256u + (size_t)max_items * sizeof(DevWork));
+        a.out = nullptr;
+        a.counter = (unsigned *)b;
+        a.err = (unsigned *)(b + 4u);
+        a.nwork = 0;
+        a.nwork_dev = (const uint32_t *)(b + 8u);
+        a.out_dev = (uint32_t *const *)(b + 16u);
+        a.buf_words = B;
+        a.persistent = 1u;
+        CUG(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        cudaError_t e1 = cudaMemsetAsync(b, 0, sizeof(unsigned), g->cap_stream);
+        cudaError_t e2 = e1 == cudaSuccess ? launch_generate(a, c.threads, c.form, qmax, grid, g->cap_stream) : e1;
+        e = cudaStreamEndCapture(g->cap_stream, &g->graph);
+        if (e2 != cudaSuccess) return bail(cuda_fail(e2, "graph: capture of the generation launch"));
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamEndCapture"));
+        CUG(cudaGraphInstantiate(&g->exec, g->graph, 0), "cudaGraphInstantiate");
+    #undef CUG
+        *out = g;
+        return MTGP_OK;
+    });
 }
 
 mtgp_status mtgp_graph_set_requests(mtgp_graph *g, const mtgp_request *reqs, uint32_t nreq, void *dev_out,
                                     mtgp_layout layout, void *stream)
 {
-    if (!g) return fail(MTGP_EINVAL, "graph is NULL");
-    mtgp_pool *p = g->pool;
-    cudaStream_t s = (cudaStream_t)stream;
-    mtgp_status st = pool_busy_check(p, s);
-    if (st != MTGP_OK) return st;
-    const mtgp_config saved = p->cfg;
-    p->cfg.persistent = 1u;                              // longest-first order for the fixed grid
-    Plan plan;
-    st = build_plan(p, reqs, nreq, layout, &plan);
-    p->cfg = saved;
-    if (st != MTGP_OK) return st;
-    if (plan.work.size() > g->max_items || plan.segs.size() > g->max_items)
-        return fail(MTGP_EINVAL, "graph: %zu work items / %zu segments exceed its capacity %u", plan.work.size(),
-                    plan.segs.size(), g->max_items);
-    if (plan.total && !dev_out) return fail(MTGP_EINVAL, "dev_out is NULL");
-    if (((uintptr_t)dev_out & 3u) != 0) return fail(MTGP_EINVAL, "dev_out must be 4-byte aligned");
-    const int k = g->slot;
-    if (g->stage_used[k]) CU(cudaEventSynchronize(g->ev_stage[k]), "cudaEventSynchronize");
-    char *h = (char *)g->h_stage[k];
-    const uint32_t nwork = (uint32_t)plan.work.size();
-    std::memcpy(h + 8u, &nwork, sizeof nwork);
-    std::memcpy(h + 16u, &dev_out, sizeof dev_out);
-    std::memcpy(h + 256u, plan.work.data(), plan.work.size() * sizeof(DevWork));
-    const size_t seg_off = 256u + (size_t)g->max_items * sizeof(DevWork);
-    std::memcpy(h + seg_off, plan.segs.data(), plan.segs.size() * sizeof(DevSeg));
-    // control words from [8, 24), then the work items, then the segments
-    CU(cudaMemcpyAsync((char *)g->d_buf + 8u, h + 8u, 248u + plan.work.size() * sizeof(DevWork),
-                       cudaMemcpyHostToDevice, s),
-       "graph: upload work list");
-    if (!plan.segs.empty())
-        CU(cudaMemcpyAsync((char *)g->d_buf + seg_off, h + seg_off, plan.segs.size() * sizeof(DevSeg),
+    return guarded([&]() -> mtgp_status {
+        if (!g) return fail(MTGP_EINVAL, "graph is NULL");
+        mtgp_pool *p = g->pool;
+        cudaStream_t s = (cudaStream_t)stream;
+        mtgp_status st = pool_busy_check(p, s);
+        if (st != MTGP_OK) return st;
+        const mtgp_config saved = p->cfg;
+        p->cfg.persistent = 1u;                              // longest-first order for the fixed grid
+        Plan plan;
+        st = build_plan(p, reqs, nreq, layout, &plan);
+        p->cfg = saved;
+        if (st != MTGP_OK) return st;
+        if (plan.work.size() > g->max_items || plan.segs.size() > g->max_items)
+            return fail(MTGP_EINVAL, "graph: %zu work items / %zu segments exceed its capacity %u", plan.work.size(),
+                        plan.segs.size(), g->max_items);
+        if (plan.total && !dev_out) return fail(MTGP_EINVAL, "dev_out is NULL");
+        if (((uintptr_t)dev_out & 3u) != 0) return fail(MTGP_EINVAL, "dev_out must be 4-byte aligned");
+        const int k = g->slot;
+        if (g->stage_used[k]) CU(cudaEventSynchronize(g->ev_stage[k]), "cudaEventSynchronize");
+        char *h = (char *)g->h_stage[k];
+        const uint32_t nwork = (uint32_t)plan.work.size();
+        std::memcpy(h + 8u, &nwork, sizeof nwork);
+        std::memcpy(h + 16u, &dev_out, sizeof dev_out);
+        std::memcpy(h + 256u, plan.work.data(), plan.work.size() * sizeof(DevWork));
+        const size_t seg_off = 256u + (size_t)g->max_items * sizeof(DevWork);
+        std::memcpy(h + seg_off, plan.segs.data(), plan.segs.size() * sizeof(DevSeg));
+        // control words from [8, 24), then the work items, then the segments
+        CU(cudaMemcpyAsync((char *)g->d_buf + 8u, h + 8u, 248u + plan.work.size() * sizeof(DevWork),
                            cudaMemcpyHostToDevice, s),
-           "graph: upload segments");
-    CU(cudaEventRecord(g->ev_stage[k], s), "cudaEventRecord");
-    g->stage_used[k] = true;
-    g->slot ^= 1;
-    p->last_stream = s;
-    CU(cudaEventRecord(p->ev_done, s), "cudaEventRecord");
-    p->used = true;
-    return MTGP_OK;
+           "graph: upload work list");
+        if (!plan.segs.empty())
+            CU(cudaMemcpyAsync((char *)g->d_buf + seg_off, h + seg_off, plan.segs.size() * sizeof(DevSeg),
+                               cudaMemcpyHostToDevice, s),
+               "graph: upload segments");
+        CU(cudaEventRecord(g->ev_stage[k], s), "cudaEventRecord");
+        g->stage_used[k] = true;
+        g->slot ^= 1;
+        p->last_stream = s;
+        CU(cudaEventRecord(p->ev_done, s), "cudaEventRecord");
+        p->used = true;
+        return MTGP_OK;
+    });
 }
 
 mtgp_status mtgp_graph_launch(mtgp_graph *g, void *stream)
@@ -1276,54 +1311,56 @@ mtgp_status mtgp_pool_launch_count(const mtgp_pool *p, uint64_t *launches)
 
 mtgp_status mtgp_pool_jump(mtgp_pool *p, uint32_t i, uint64_t steps, void *stream)
 {
-    if (!p || i >= p->count) return fail(MTGP_EINVAL, "bad pool or generator index");
-    cudaStream_t s = (cudaStream_t)stream;
-    mtgp_status st = pool_busy_check(p, s);
-    if (st != MTGP_OK) return st;
-    if (steps == 0) return MTGP_OK;
-    int r = jump_annihilate(p->jc, p->host_gens.data(), p->d_gens, p->d_state, &i, 1u, s);
-    if (r != MTGP_OK) return (mtgp_status)r;
-    if (p->jc.dev_bytes > kJumpStoreCap) {
-        st = pool_sync(p);
+    return guarded([&]() -> mtgp_status {
+        if (!p || i >= p->count) return fail(MTGP_EINVAL, "bad pool or generator index");
+        cudaStream_t s = (cudaStream_t)stream;
+        mtgp_status st = pool_busy_check(p, s);
         if (st != MTGP_OK) return st;
-        jump_clear(p->jc, false);
-    }
-    r = jump_polys(p->jc, {{i, steps}});
-    if (r != MTGP_OK) return (mtgp_status)r;
-    const JumpPoly jp = jump_poly(p->jc, i, steps);
-    const DevGen &g = p->host_gens[i];
-    DevJump jb{};
-    jb.poly = jp.d;
-    jb.ncoef = jp.ncoef;
-    jb.src = g.state_off;
-    jb.dst = g.state_off;                 // in place: the walk reads the state first
-    jb.gen = i;
-    jb.nseq = jump_seq_words(g.N, jb.ncoef);
-    jb.mode = kJumpStep;
-    st = ensure_upload_space(p, sizeof jb);
-    if (st != MTGP_OK) return st;
-    const bool fused = jump_fused_fits(g.N, jb.nseq, jb.ncoef);
-    st = ensure_jump_space(p, 0u, fused ? 0u : jb.nseq);
-    if (st != MTGP_OK) return st;
-    std::memcpy(p->h_stage, &jb, sizeof jb);
-    CU(cudaMemcpyAsync(p->d_work, p->h_stage, sizeof jb, cudaMemcpyHostToDevice, s), "upload jump job");
-    if (fused) {                          // in place: the block reads the whole state before writing
-        CU(launch_jump_fused(p->d_gens, p->d_state, p->d_state, (const DevJump *)p->d_work, 1u, g.N, jb.nseq,
-                             jb.ncoef, s),
-           "jump kernel launch");
-    } else {
-        CU(launch_walk(p->d_gens, p->d_state, p->d_seq, (const DevJump *)p->d_work, 1u, g.N, s),
-           "walk kernel launch");
-        CU(launch_jump_sum(p->d_gens, p->d_seq, p->d_state, (const DevJump *)p->d_work, 1u, g.N, s),
-           "jump kernel launch");
-    }
-    CU(cudaStreamSynchronize(s), "jump");
-    uint64_t pos = 0;
-    char *cnt = (char *)p->d_gens + sizeof(DevGen) * i + offsetof(DevGen, count);
-    CU(cudaMemcpy(&pos, cnt, sizeof pos, cudaMemcpyDeviceToHost), "read position");
-    pos += steps;
-    CU(cudaMemcpy(cnt, &pos, sizeof pos, cudaMemcpyHostToDevice), "write position");
-    return MTGP_OK;
+        if (steps == 0) return MTGP_OK;
+        int r = jump_annihilate(p->jc, p->host_gens.data(), p->d_gens, p->d_state, &i, 1u, s);
+        if (r != MTGP_OK) return (mtgp_status)r;
+        if (p->jc.dev_bytes > kJumpStoreCap) {
+            st = pool_sync(p);
+            if (st != MTGP_OK) return st;
+            jump_clear(p->jc, false);
+        }
+        r = jump_polys(p->jc, {{i, steps}});
+        if (r != MTGP_OK) return (mtgp_status)r;
+        const JumpPoly jp = jump_poly(p->jc, i, steps);
+        const DevGen &g = p->host_gens[i];
+        DevJump jb{};
+        jb.poly = jp.d;
+        jb.ncoef = jp.ncoef;
+        jb.src = g.state_off;
+        jb.dst = g.state_off;                 // in place: the walk reads the state first
+        jb.gen = i;
+        jb.nseq = jump_seq_words(g.N, jb.ncoef);
+        jb.mode = kJumpStep;
+        st = ensure_upload_space(p, sizeof jb);
+        if (st != MTGP_OK) return st;
+        const bool fused = jump_fused_fits(g.N, jb.nseq, jb.ncoef);
+        st = ensure_jump_space(p, 0u, fused ? 0u : jb.nseq);
+        if (st != MTGP_OK) return st;
+        std::memcpy(p->h_stage, &jb, sizeof jb);
+        CU(cudaMemcpyAsync(p->d_work, p->h_stage, sizeof jb, cudaMemcpyHostToDevice, s), "upload jump job");
+        if (fused) {                          // in place: the block reads the whole state before writing
+            CU(launch_jump_fused(p->d_gens, p->d_state, p->d_state, (const DevJump *)p->d_work, 1u, g.N, jb.nseq,
+                                 jb.ncoef, s),
+               "jump kernel launch");
+        } else {
+            CU(launch_walk(p->d_gens, p->d_state, p->d_seq, (const DevJump *)p->d_work, 1u, g.N, s),
+               "walk kernel launch");
+            CU(launch_jump_sum(p->d_gens, p->d_seq, p->d_state, (const DevJump *)p->d_work, 1u, g.N, s),
+               "jump kernel launch");
+        }
+        CU(cudaStreamSynchronize(s), "jump");
+        uint64_t pos = 0;
+        char *cnt = (char *)p->d_gens + sizeof(DevGen) * i + offsetof(DevGen, count);
+        CU(cudaMemcpy(&pos, cnt, sizeof pos, cudaMemcpyDeviceToHost), "read position");
+        pos += steps;
+        CU(cudaMemcpy(cnt, &pos, sizeof pos, cudaMemcpyHostToDevice), "write position");
+        return MTGP_OK;
+    });
 }
 
 mtgp_status mtgp_state_jump(mtgp_state *s, uint64_t steps, void *stream)
@@ -1335,21 +1372,23 @@ mtgp_status mtgp_state_jump(mtgp_state *s, uint64_t steps, void *stream)
 mtgp_status mtgp_pool_annihilator(mtgp_pool *p, uint32_t i, uint64_t *poly, uint32_t poly_words,
                                   uint32_t *degree, void *stream)
 {
-    if (!p || i >= p->count || !degree) return fail(MTGP_EINVAL, "bad pool, index or NULL degree");
-    cudaStream_t s = (cudaStream_t)stream;
-    mtgp_status st = pool_busy_check(p, s);
-    if (st != MTGP_OK) return st;
-    const int r = jump_annihilate(p->jc, p->host_gens.data(), p->d_gens, p->d_state, &i, 1u, s);
-    if (r != MTGP_OK) return (mtgp_status)r;
-    const f2::Poly &a = p->jc.ann[i];
-    const int64_t d = f2::degree(a);
-    *degree = (uint32_t)std::max<int64_t>(d, 0);
-    if (!poly) return MTGP_OK;
-    const size_t need = (size_t)(*degree / 64u) + 1u;
-    if (poly_words < need) return fail(MTGP_EINVAL, "poly has %u words, need %zu", poly_words, need);
-    std::memset(poly, 0, sizeof(uint64_t) * poly_words);
-    std::copy(a.begin(), a.end(), poly);
-    return MTGP_OK;
+    return guarded([&]() -> mtgp_status {
+        if (!p || i >= p->count || !degree) return fail(MTGP_EINVAL, "bad pool, index or NULL degree");
+        cudaStream_t s = (cudaStream_t)stream;
+        mtgp_status st = pool_busy_check(p, s);
+        if (st != MTGP_OK) return st;
+        const int r = jump_annihilate(p->jc, p->host_gens.data(), p->d_gens, p->d_state, &i, 1u, s);
+        if (r != MTGP_OK) return (mtgp_status)r;
+        const f2::Poly &a = p->jc.ann[i];
+        const int64_t d = f2::degree(a);
+        *degree = (uint32_t)std::max<int64_t>(d, 0);
+        if (!poly) return MTGP_OK;
+        const size_t need = (size_t)(*degree / 64u) + 1u;
+        if (poly_words < need) return fail(MTGP_EINVAL, "poly has %u words, need %zu", poly_words, need);
+        std::memset(poly, 0, sizeof(uint64_t) * poly_words);
+        std::copy(a.begin(), a.end(), poly);
+        return MTGP_OK;
+    });
 }
 
 }  // extern "C"

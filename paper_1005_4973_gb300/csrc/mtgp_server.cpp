@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cstdio>
 #include <deque>
+#include <exception>
 #include <map>
 #include <new>
 #include <unordered_map>
@@ -36,6 +37,20 @@ mtgp_status fail_cuda(cudaError_t e, const char *what)
     char buf[256];
     snprintf(buf, sizeof buf, "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
     return fail(MTGP_ECUDA, buf);
+}
+
+// Entry points return MTGP_ENOMEM instead of letting a container's
+// allocation failure cross the C ABI.
+template <class F>
+mtgp_status guarded(F &&f)
+{
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        return fail(MTGP_ENOMEM, "server: host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(MTGP_EINVAL, e.what());
+    }
 }
 
 constexpr uint64_t kAlign = 256;
@@ -108,67 +123,71 @@ extern "C" {
 
 mtgp_status mtgp_server_create(mtgp_pool *pool, const mtgp_server_config *cfg, void *stream, mtgp_server **out)
 {
-    if (!pool || !out) return fail(MTGP_EINVAL, "server: NULL pool or out");
-    *out = nullptr;
-    mtgp_server *s = new (std::nothrow) mtgp_server;
-    if (!s) return fail(MTGP_ENOMEM, "host allocation");
-    s->pool = pool;
-    s->stream = (cudaStream_t)stream;
-    if (cfg) s->cfg = *cfg;
-    if (!s->cfg.arena_bytes) s->cfg.arena_bytes = 1ull << 32;
-    if (!s->cfg.chunk) s->cfg.chunk = 1ull << 20;
-    if (!s->cfg.max_active) s->cfg.max_active = 4096;
-    if (!s->cfg.max_inflight) s->cfg.max_inflight = 2;
-    s->cfg.arena_bytes = s->cfg.arena_bytes / kAlign * kAlign;
-    uint64_t dev_bytes = 0;
-    mtgp_status st = mtgp_pool_info(pool, &s->count, &dev_bytes);
-    if (st != MTGP_OK) {
-        delete s;
-        return st;
-    }
-    s->gen_busy.assign(s->count, 0);
-    cudaError_t e = cudaMalloc(&s->arena, s->cfg.arena_bytes);
-    if (e != cudaSuccess) {
-        delete s;
-        return e == cudaErrorMemoryAllocation ? fail(MTGP_ENOMEM, "server: arena allocation")
-                                              : fail_cuda(e, "server: cudaMalloc arena");
-    }
-    s->free_list[0] = s->cfg.arena_bytes;
-    st = mtgp_graph_create(pool, std::min<uint32_t>(s->cfg.max_active, s->count), stream, &s->graph);
-    if (st != MTGP_OK) {
-        mtgp_server_destroy(s);
-        return st;
-    }
-    e = cudaEventCreate(&s->ev_ref);
-    if (e == cudaSuccess) e = cudaEventRecord(s->ev_ref, s->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(s->ev_ref);
-    if (e != cudaSuccess) {
-        mtgp_server_destroy(s);
-        return fail_cuda(e, "server: reference event");
-    }
-    s->t0 = std::chrono::steady_clock::now();
-    *out = s;
-    return MTGP_OK;
+    return guarded([&]() -> mtgp_status {
+        if (!pool || !out) return fail(MTGP_EINVAL, "server: NULL pool or out");
+        *out = nullptr;
+        mtgp_server *s = new (std::nothrow) mtgp_server;
+        if (!s) return fail(MTGP_ENOMEM, "host allocation");
+        s->pool = pool;
+        s->stream = (cudaStream_t)stream;
+        if (cfg) s->cfg = *cfg;
+        if (!s->cfg.arena_bytes) s->cfg.arena_bytes = 1ull << 32;
+        if (!s->cfg.chunk) s->cfg.chunk = 1ull << 20;
+        if (!s->cfg.max_active) s->cfg.max_active = 4096;
+        if (!s->cfg.max_inflight) s->cfg.max_inflight = 2;
+        s->cfg.arena_bytes = s->cfg.arena_bytes / kAlign * kAlign;
+        uint64_t dev_bytes = 0;
+        mtgp_status st = mtgp_pool_info(pool, &s->count, &dev_bytes);
+        if (st != MTGP_OK) {
+            delete s;
+            return st;
+        }
+        s->gen_busy.assign(s->count, 0);
+        cudaError_t e = cudaMalloc(&s->arena, s->cfg.arena_bytes);
+        if (e != cudaSuccess) {
+            delete s;
+            return e == cudaErrorMemoryAllocation ? fail(MTGP_ENOMEM, "server: arena allocation")
+                                                  : fail_cuda(e, "server: cudaMalloc arena");
+        }
+        s->free_list[0] = s->cfg.arena_bytes;
+        st = mtgp_graph_create(pool, std::min<uint32_t>(s->cfg.max_active, s->count), stream, &s->graph);
+        if (st != MTGP_OK) {
+            mtgp_server_destroy(s);
+            return st;
+        }
+        e = cudaEventCreate(&s->ev_ref);
+        if (e == cudaSuccess) e = cudaEventRecord(s->ev_ref, s->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(s->ev_ref);
+        if (e != cudaSuccess) {
+            mtgp_server_destroy(s);
+            return fail_cuda(e, "server: reference event");
+        }
+        s->t0 = std::chrono::steady_clock::now();
+        *out = s;
+        return MTGP_OK;
+    });
 }
 
 mtgp_status mtgp_server_submit(mtgp_server *s, uint32_t gen, uint32_t dtype, uint64_t n, uint64_t *ticket)
 {
-    if (!s || !ticket) return fail(MTGP_EINVAL, "server: NULL argument");
-    if (gen >= s->count) return fail(MTGP_EINVAL, "server: generator out of range");
-    if (dtype > 2u) return fail(MTGP_EINVAL, "server: unknown dtype");
-    if (n == 0) return fail(MTGP_EINVAL, "server: empty request");
-    if (4u * n > s->cfg.arena_bytes) return fail(MTGP_EINVAL, "server: request larger than the arena");
-    Req r;
-    r.gen = gen;
-    r.dtype = dtype;
-    r.n = n;
-    r.bytes = 4u * n;
-    r.submit_s = s->now_s();
-    const uint64_t t = s->next_ticket++;
-    s->reqs[t] = r;
-    s->pending.push_back(t);
-    *ticket = t;
-    return MTGP_OK;
+    return guarded([&]() -> mtgp_status {
+        if (!s || !ticket) return fail(MTGP_EINVAL, "server: NULL argument");
+        if (gen >= s->count) return fail(MTGP_EINVAL, "server: generator out of range");
+        if (dtype > 2u) return fail(MTGP_EINVAL, "server: unknown dtype");
+        if (n == 0) return fail(MTGP_EINVAL, "server: empty request");
+        if (4u * n > s->cfg.arena_bytes) return fail(MTGP_EINVAL, "server: request larger than the arena");
+        Req r;
+        r.gen = gen;
+        r.dtype = dtype;
+        r.n = n;
+        r.bytes = 4u * n;
+        r.submit_s = s->now_s();
+        const uint64_t t = s->next_ticket++;
+        s->reqs[t] = r;
+        s->pending.push_back(t);
+        *ticket = t;
+        return MTGP_OK;
+    });
 }
 
 }  // extern "C"
@@ -281,38 +300,42 @@ extern "C" {
 
 mtgp_status mtgp_server_poll(mtgp_server *s, mtgp_completion *done, uint32_t max, uint32_t *ndone, int block)
 {
-    if (!s || !ndone || (max && !done)) return fail(MTGP_EINVAL, "server: NULL argument");
-    *ndone = 0;
-    mtgp_status st = retire(s, false);
-    if (st != MTGP_OK) return st;
-    admit(s);
-    bool launched = false;
-    if (!s->active.empty() && s->inflight.size() < s->cfg.max_inflight) {
-        st = launch_tick(s);
-        if (st != MTGP_OK) return st;
-        launched = true;
-    }
-    if (block && !launched && s->done_q.empty() && !s->inflight.empty()) {
-        st = retire(s, true);
+    return guarded([&]() -> mtgp_status {
+        if (!s || !ndone || (max && !done)) return fail(MTGP_EINVAL, "server: NULL argument");
+        *ndone = 0;
+        mtgp_status st = retire(s, false);
         if (st != MTGP_OK) return st;
         admit(s);
-    }
-    while (*ndone < max && !s->done_q.empty()) {
-        done[(*ndone)++] = s->done_q.front();
-        s->done_q.pop_front();
-    }
-    return MTGP_OK;
+        bool launched = false;
+        if (!s->active.empty() && s->inflight.size() < s->cfg.max_inflight) {
+            st = launch_tick(s);
+            if (st != MTGP_OK) return st;
+            launched = true;
+        }
+        if (block && !launched && s->done_q.empty() && !s->inflight.empty()) {
+            st = retire(s, true);
+            if (st != MTGP_OK) return st;
+            admit(s);
+        }
+        while (*ndone < max && !s->done_q.empty()) {
+            done[(*ndone)++] = s->done_q.front();
+            s->done_q.pop_front();
+        }
+        return MTGP_OK;
+    });
 }
 
 mtgp_status mtgp_server_release(mtgp_server *s, uint64_t ticket)
 {
-    if (!s) return fail(MTGP_EINVAL, "server: NULL server");
-    auto it = s->reqs.find(ticket);
-    if (it == s->reqs.end()) return fail(MTGP_EINVAL, "server: unknown ticket");
-    if (!it->second.finished) return fail(MTGP_EBUSY, "server: request not completed yet");
-    s->release_range(it->second.off, it->second.bytes);
-    s->reqs.erase(it);
-    return MTGP_OK;
+    return guarded([&]() -> mtgp_status {
+        if (!s) return fail(MTGP_EINVAL, "server: NULL server");
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return fail(MTGP_EINVAL, "server: unknown ticket");
+        if (!it->second.finished) return fail(MTGP_EBUSY, "server: request not completed yet");
+        s->release_range(it->second.off, it->second.bytes);
+        s->reqs.erase(it);
+        return MTGP_OK;
+    });
 }
 
 mtgp_status mtgp_server_stats(const mtgp_server *s, mtgp_server_stats_t *out)
@@ -350,34 +373,36 @@ extern "C" mtgp_status mtgp_server_run_trace(mtgp_server *s, const double *arriv
                                              const uint32_t *dtypes, const uint64_t *ns, uint32_t count,
                                              double *latency_s, double *done_s)
 {
-    if (!s || (count && (!arrival_s || !gens || !dtypes || !ns || !latency_s))) return fail(MTGP_EINVAL, "trace: NULL argument");
-    std::unordered_map<uint64_t, uint32_t> index;     // ticket -> position in the trace
-    index.reserve(count * 2u + 1u);
-    std::vector<mtgp_completion> buf(1024);
-    const double start = s->now_s();
-    uint32_t next = 0, finished = 0;
-    for (uint32_t i = 0; i < count; ++i)
-        if (i && arrival_s[i] < arrival_s[i - 1]) return fail(MTGP_EINVAL, "trace: arrival times must not decrease");
-    while (finished < count) {
-        const double now = s->now_s() - start;
-        while (next < count && arrival_s[next] <= now) {
-            uint64_t t = 0;
-            mtgp_status st = mtgp_server_submit(s, gens[next], dtypes[next], ns[next], &t);
+    return guarded([&]() -> mtgp_status {
+        if (!s || (count && (!arrival_s || !gens || !dtypes || !ns || !latency_s))) return fail(MTGP_EINVAL, "trace: NULL argument");
+        std::unordered_map<uint64_t, uint32_t> index;     // ticket -> position in the trace
+        index.reserve(count * 2u + 1u);
+        std::vector<mtgp_completion> buf(1024);
+        const double start = s->now_s();
+        uint32_t next = 0, finished = 0;
+        for (uint32_t i = 0; i < count; ++i)
+            if (i && arrival_s[i] < arrival_s[i - 1]) return fail(MTGP_EINVAL, "trace: arrival times must not decrease");
+        while (finished < count) {
+            const double now = s->now_s() - start;
+            while (next < count && arrival_s[next] <= now) {
+                uint64_t t = 0;
+                mtgp_status st = mtgp_server_submit(s, gens[next], dtypes[next], ns[next], &t);
+                if (st != MTGP_OK) return st;
+                index[t] = next++;
+            }
+            uint32_t nd = 0;
+            mtgp_status st = mtgp_server_poll(s, buf.data(), (uint32_t)buf.size(), &nd, next == count ? 1 : 0);
             if (st != MTGP_OK) return st;
-            index[t] = next++;
+            for (uint32_t j = 0; j < nd; ++j) {
+                const uint32_t i = index[buf[j].ticket];
+                latency_s[i] = buf[j].done_s - buf[j].submit_s;
+                if (done_s) done_s[i] = buf[j].done_s - start;
+                index.erase(buf[j].ticket);
+                st = mtgp_server_release(s, buf[j].ticket);
+                if (st != MTGP_OK) return st;
+                ++finished;
+            }
         }
-        uint32_t nd = 0;
-        mtgp_status st = mtgp_server_poll(s, buf.data(), (uint32_t)buf.size(), &nd, next == count ? 1 : 0);
-        if (st != MTGP_OK) return st;
-        for (uint32_t j = 0; j < nd; ++j) {
-            const uint32_t i = index[buf[j].ticket];
-            latency_s[i] = buf[j].done_s - buf[j].submit_s;
-            if (done_s) done_s[i] = buf[j].done_s - start;
-            index.erase(buf[j].ticket);
-            st = mtgp_server_release(s, buf[j].ticket);
-            if (st != MTGP_OK) return st;
-            ++finished;
-        }
-    }
-    return MTGP_OK;
+        return MTGP_OK;
+    });
 }

@@ -92,6 +92,8 @@ def lib():
             "orc_search_full_period": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
                                                       ctypes.c_int, P(OrcParams), u64p]),
             "orc_params_sizeof": (ctypes.c_int, []),
+            "orc_kv": (ctypes.c_int, [u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_int)]),
+            "orc_mt19937_outputs": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, u32p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -248,6 +250,32 @@ def search_full_period(mexp: int, seed0: int, gen_id: int, max_tries: int = 2000
     if t < 0:
         raise RuntimeError(f"no full-period set for mexp={mexp} in {max_tries} tries")
     return p, found.value, t
+
+
+# --------------------------------------------------------------------------
+# dimensions of equidistribution (Sec. 3.4, 3.8)
+# --------------------------------------------------------------------------
+def kv(seq: np.ndarray, p: int, vmax: int = 32) -> np.ndarray:
+    """k(v), v = 1..vmax, of the 32-bit output sequence seq (from a nonzero
+    state of a full-period generator of state dimension p)."""
+    seq = np.ascontiguousarray(seq, dtype=np.uint32)
+    out = (ctypes.c_int * vmax)()
+    if lib().orc_kv(_p(seq, ctypes.c_uint32), seq.size, p, vmax, out):
+        raise MemoryError("oracle allocation failed")
+    return np.array(list(out), dtype=np.int64)
+
+
+def mt19937_outputs(seed: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.uint32)
+    if lib().orc_mt19937_outputs(seed, n, _p(out, ctypes.c_uint32)):
+        raise MemoryError("oracle allocation failed")
+    return out
+
+
+def dimension_defects(k: np.ndarray, p: int) -> np.ndarray:
+    """d(v) = floor(p / v) - k(v) (Sec. 3.4)."""
+    v = np.arange(1, k.size + 1)
+    return p // v - k
 
 
 # --------------------------------------------------------------------------

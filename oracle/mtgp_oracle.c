@@ -17,6 +17,12 @@
  *                                      paper leaves open: parity unpinned against any
  *                                      outside source (checked for structure only)
  *   orc_bm / orc_poly_*                pinned against closed forms and brute force
+ *   orc_kv                             pinned by the dimension defects the paper
+ *                                      prints for MT19937 (Sec. 3.8), the bound
+ *                                      k(v) <= floor(p / v) and k(1) = p at full
+ *                                      period
+ *   orc_mt19937_outputs                the published MT19937 (Matsumoto and
+ *                                      Nishimura 1998), only as the k(v) pin's input
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -506,6 +512,87 @@ int orc_search_full_period(uint32_t mexp, uint64_t seed0, uint32_t id, int max_t
     }
     free(bits); free(poly);
     return ret;
+}
+
+/* ---- dimensions of equidistribution (Sec. 3.4, 3.8) ---------------------- */
+
+/*
+ * k(v) for v = 1 .. vmax of a 32-bit output sequence seq[0 .. L) of an
+ * F2-linear generator with state dimension p, period 2^p - 1 and seq taken
+ * from a nonzero state s.  The v-bit MSB sequence is k-dimensionally
+ * equidistributed iff the linear map from states to the v MSBs of k
+ * consecutive outputs is onto, i.e. has rank k v.  The states F^j s
+ * (j = 0 .. p-1) form a basis (s is cyclic at full period), so the map's
+ * matrix in that basis has the row (i, b) = bit b of seq[i + j], j < p.
+ * Rows are added output by output (v rows each, MSB first) to a row-echelon
+ * basis kept by lowest set bit; k(v) is the number of outputs before the
+ * first dependent row.  Needs L >= p + floor(p / v) + 1.  Returns 0, or -1
+ * on allocation failure.
+ */
+int orc_kv(const uint32_t *seq, int L, int p, int vmax, int *kv)
+{
+    const int W = (p + 63) / 64;
+    uint64_t *basis = (uint64_t *)malloc((size_t)p * (size_t)W * 8u);
+    int *piv = (int *)malloc((size_t)p * sizeof(int));
+    uint64_t *row = (uint64_t *)malloc((size_t)W * 8u);
+    if (!basis || !piv || !row) { free(basis); free(piv); free(row); return -1; }
+    for (int v = 1; v <= vmax; v++) {
+        for (int c = 0; c < p; c++) piv[c] = -1;
+        int rank = 0, k = 0, dependent = 0;
+        for (int i = 0; !dependent && i + p <= L; i++) {
+            for (int b = 31; b > 31 - v && !dependent; b--) {
+                memset(row, 0, (size_t)W * 8u);
+                for (int j = 0; j < p; j++)
+                    if ((seq[i + j] >> b) & 1u) row[j >> 6] |= 1ull << (j & 63);
+                for (;;) {
+                    int c = -1;
+                    for (int w = 0; w < W; w++)
+                        if (row[w]) { c = 64 * w + __builtin_ctzll(row[w]); break; }
+                    if (c < 0) { dependent = 1; break; }
+                    if (piv[c] < 0) {
+                        memcpy(basis + (size_t)rank * W, row, (size_t)W * 8u);
+                        piv[c] = rank++;
+                        break;
+                    }
+                    const uint64_t *r = basis + (size_t)piv[c] * W;
+                    for (int w = 0; w < W; w++) row[w] ^= r[w];
+                }
+            }
+            if (!dependent) k = i + 1;
+        }
+        kv[v - 1] = k;
+    }
+    free(basis); free(piv); free(row);
+    return 0;
+}
+
+/*
+ * The published MT19937 (Matsumoto and Nishimura, ACM TOMACS 1998): N = 624,
+ * M = 397, r = 31 (one upper bit of x_i joins the 31 lower bits of x_{i+1}),
+ * twist vector 0x9908b0df; tempering shifts 11, 7, 15, 18 with masks
+ * 0x9d2c5680 and 0xefc60000.  State filled by SplitMix64 from `seed` (any
+ * nonzero state will do for orc_kv).  Straight array, n outputs.
+ */
+int orc_mt19937_outputs(uint64_t seed, int n, uint32_t *out)
+{
+    const int N = 624, M = 397;
+    uint32_t *x = (uint32_t *)malloc(((size_t)N + (size_t)n) * 4u);
+    if (!x) return -1;
+    uint64_t s = seed;
+    for (int j = 0; j < N; j++) x[j] = (uint32_t)orc_splitmix64_next(&s);
+    x[0] |= 0x80000000u;                          /* the upper bit of x_0 is state: nonzero */
+    for (int i = 0; i < n; i++) {
+        const uint32_t y = (x[i] & 0x80000000u) | (x[i + 1] & 0x7fffffffu);
+        x[N + i] = x[i + M] ^ (y >> 1) ^ ((y & 1u) ? 0x9908b0dfu : 0u);
+        uint32_t z = x[N + i];
+        z ^= z >> 11;
+        z ^= (z << 7) & 0x9d2c5680u;
+        z ^= (z << 15) & 0xefc60000u;
+        z ^= z >> 18;
+        out[i] = z;
+    }
+    free(x);
+    return 0;
 }
 
 /* Size of the parameter struct, so the Python side can check its mirror. */

@@ -108,6 +108,7 @@ _SIGS = {
     "mtgp_pool_annihilator": (ctypes.c_int, [_vp, _u32, _P(_u64), _u32, _P(_u32), _vp]),
     "mtgp_params_search": (ctypes.c_int, [_u32, _u64, _u32, _u64, _u32, _P(mtgp_params), _P(_u64), _P(_u64),
                                           _P(_u64), _u32]),
+    "mtgp_params_equidistribution": (ctypes.c_int, [_P(mtgp_params), _u32, _P(_u32), _P(_u32)]),
     "mtgp_f2_minpoly": (ctypes.c_int, [_P(_u64), _u64, _P(_u64), _u32, _P(ctypes.c_int64)]),
     "mtgp_f2_mulmod": (ctypes.c_int, [_P(_u64), _u32, _P(_u64), _u32, _P(_u64), _u32, _P(_u64), _u32,
                                       _P(ctypes.c_int64)]),

@@ -35,6 +35,15 @@ def mtgp_params_search(mexp: int, seed0: int, gen_id: int, max_tries: int = 1 <<
     return p, found.value, tries.value, poly_from_words(words, mexp)
 
 
+def mtgp_params_equidistribution(p: mtgp_params, threads: int = 0):
+    """k(v) for v = 1..32 (index v - 1) and the total dimension defect
+    (Sec. 3.4, 3.8) of a full-period parameter set."""
+    kv = (ctypes.c_uint32 * 32)()
+    delta = ctypes.c_uint32()
+    L.check(L.LIB.mtgp_params_equidistribution(ctypes.byref(p), threads, kv, ctypes.byref(delta)))
+    return np.array(list(kv), dtype=np.int64), delta.value
+
+
 def mtgpdc_record(p: mtgp_params, charpoly) -> str:
     """One comma-separated record of a searched set, with the additional data
     Sec. 5 lists: SHA1 of the characteristic polynomial (its coefficients as

@@ -191,6 +191,18 @@ mtgp_status mtgp_params_search(uint32_t mexp, uint64_t seed0, uint32_t id, uint6
  */
 mtgp_status mtgp_params_equidistribution(const mtgp_params *p, uint32_t threads, uint32_t *kv, uint32_t *delta);
 
+/*
+ * Tempering search (Sec. 5: MTGPDC searches a tempering set once the
+ * recursion set is found; the paper does not say how): candidate 0 is the
+ * input's tmp_tbl, candidate t = 1 .. tries the table of four random rows
+ * (SplitMix64 from seed + t, Sec. 3.7 table convention).  *out = the input
+ * with the table of the smallest total dimension defect (earliest on ties),
+ * that defect to *delta (if not NULL).  Each candidate costs one
+ * mtgp_params_equidistribution.  For full-period sets.
+ */
+mtgp_status mtgp_params_temper_search(const mtgp_params *in, uint64_t seed, uint32_t tries, uint32_t threads,
+                                      mtgp_params *out, uint32_t *delta);
+
 /* ---- single generator (Sec. 8 host/kernel flow) --------------------------- */
 
 /*

@@ -109,6 +109,7 @@ _SIGS = {
     "mtgp_params_search": (ctypes.c_int, [_u32, _u64, _u32, _u64, _u32, _P(mtgp_params), _P(_u64), _P(_u64),
                                           _P(_u64), _u32]),
     "mtgp_params_equidistribution": (ctypes.c_int, [_P(mtgp_params), _u32, _P(_u32), _P(_u32)]),
+    "mtgp_params_temper_search": (ctypes.c_int, [_P(mtgp_params), _u64, _u32, _u32, _P(mtgp_params), _P(_u32)]),
     "mtgp_f2_minpoly": (ctypes.c_int, [_P(_u64), _u64, _P(_u64), _u32, _P(ctypes.c_int64)]),
     "mtgp_f2_mulmod": (ctypes.c_int, [_P(_u64), _u32, _P(_u64), _u32, _P(_u64), _u32, _P(_u64), _u32,
                                       _P(ctypes.c_int64)]),

@@ -100,3 +100,25 @@ def test_library_kv_equals_the_oracle(M, mexp, s0, gid):
     assert delta == int(O.dimension_defects(ko, mexp).sum())
     k1, _ = M.mtgp_params_equidistribution(p, threads=1)
     assert np.array_equal(k1, k)
+
+
+def test_tempering_search_lowers_the_defect_and_matches_the_oracle(M):
+    """The tempering search keeps the recursion, never returns a worse total
+    defect than the input's, and the oracle's k(v) for the returned table
+    (rebuilt from its four rows, Sec. 3.7 convention) equals the library's."""
+    p, seed, _, _ = M.mtgp_params_search(1279, 9, 1)
+    _, d0 = M.mtgp_params_equidistribution(p)
+    q, d1 = M.mtgp_params_temper_search(p, 100, 40)
+    assert d1 <= d0
+    assert list(q.rec_tbl) == list(p.rec_tbl) and q.pos == p.pos
+    M.mtgp_params_validate(q)
+    kq, dq = M.mtgp_params_equidistribution(q)
+    assert dq == d1
+    rows_r = [p.rec_tbl[8], p.rec_tbl[4], p.rec_tbl[2], p.rec_tbl[1]]
+    rows_t = [q.tmp_tbl[8], q.tmp_tbl[4], q.tmp_tbl[2], q.tmp_tbl[1]]
+    oq = O.params_from_fields(q.mexp, q.pos, q.sh1, q.sh2, q.id, rows_r, rows_t)
+    assert list(oq.rectbl) == list(q.rec_tbl) and list(oq.tmptbl) == list(q.tmp_tbl)
+    ko = O.kv(O.generate(oq, O.seed_state(oq, 2, 3), 2 * 1279 + 64, 0), 1279)
+    assert np.array_equal(kq, ko)
+    table = M.equidistribution_table(q, kq)
+    assert table.splitlines()[-1] == f"total dimension defect {d1}"

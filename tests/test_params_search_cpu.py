@@ -53,7 +53,9 @@ def test_search_limits_and_record(M):
         M.mtgp_params_search(1279, 9, 1, max_tries=3)      # the first accepted candidate is number 1184
     p, seed, tries, phi = M.mtgp_params_search(89, 1000, 7)
     rec = M.mtgpdc_record(p, phi).split(",")
-    assert rec[0] == "89" and len(rec) == 6 + 32 + 2 and len(rec[-2]) == 40 and int(rec[-1]) == int(phi.sum())
+    _, delta = M.mtgp_params_equidistribution(p)
+    assert rec[0] == "89" and len(rec) == 6 + 32 + 3 and len(rec[-3]) == 40
+    assert int(rec[-2]) == int(phi.sum()) and int(rec[-1]) == delta
 
 
 @pytest.mark.manual

@@ -56,8 +56,6 @@ __device__ __forceinline__ void round_sync()
 // dependency chains interleave: all shared loads, the recursion up to the
 // table look-up (Sec. 3.6), the look-ups, the tempering (Sec. 3.7), then the
 // stores.  x points at this thread's x_{rS+tid}, out at its output slot.
-// Outputs go out with plain stores (measured as fast as streaming stores on
-// C2 and 3 % faster on C4).
 // When QN = Q the last slot is the round's tail and only lanes with
 // last_lane set keep its result.
 template <int T, int Q, int QN, int DT>
@@ -94,7 +92,7 @@ __device__ __forceinline__ void round_slots(const GenCtx &g, uint32_t *x, uint32
             if (q + 1 < QN || QN < Q || last_lane) {
                 xn_p[q * T] = xn;
                 prev[q] = xn;
-                out[q * T] = finish(DT, xn ^ c[q]);
+                __stcs(out + q * T, finish(DT, xn ^ c[q]));
             }
         }
     }
@@ -136,7 +134,7 @@ __device__ __forceinline__ void round_fast(const GenCtx &g, uint32_t *x, uint32_
         if (tail_lane) {
             xn_p[q * T] = xn;
             prev[q] = xn;
-            out[q * T] = finish(DT, xn ^ v);
+            __stcs(out + q * T, finish(DT, xn ^ v));
         }
     }
 }

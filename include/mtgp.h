@@ -119,7 +119,8 @@ typedef struct mtgp_config {
                                   launch; outputs are identical.  0 = auto (about 16
                                   blocks per SM), 1 = never split                    */
     uint32_t piece_log2;       /* pieces hold at least 2^piece_log2 numbers; 0 = 20,
-                                  else 10 .. 40                                      */
+                                  else 10 .. 40.  Calls on a stream that is being
+                                  captured into a CUDA graph are not split        */
 } mtgp_config;
 
 /* ---- library ------------------------------------------------------------ */

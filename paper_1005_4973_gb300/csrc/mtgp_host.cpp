@@ -434,6 +434,11 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
 {
     const mtgp_config &c = p->cfg;
     if (c.pieces == 1u || plan->work.empty()) return MTGP_OK;
+    // the annihilators and polynomials may need synchronous GPU work and
+    // copies, which a stream being captured into a graph cannot take
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(s, &cap), "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone) return MTGP_OK;
     const uint64_t min_piece = 1ull << (c.piece_log2 ? c.piece_log2 : 20u);
     // auto: pieces of about Lt = total / (16 SMs) numbers, so that the launch
     // has about 16 equal shares of work per SM and long items stop setting its

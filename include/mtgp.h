@@ -119,8 +119,7 @@ typedef struct mtgp_config {
                                   launch; outputs are identical.  0 = auto (about 16
                                   blocks per SM), 1 = never split                    */
     uint32_t piece_log2;       /* pieces hold at least 2^piece_log2 numbers; 0 = 20,
-                                  else 10 .. 40.  Calls on a stream that is being
-                                  captured into a CUDA graph are not split        */
+                                  else 10 .. 40                                    */
 } mtgp_config;
 
 /* ---- library ------------------------------------------------------------ */
@@ -263,17 +262,22 @@ mtgp_status mtgp_pool_get_config(const mtgp_pool *p, mtgp_config *cfg);
 mtgp_status mtgp_pool_set_config(mtgp_pool *p, const mtgp_config *cfg);
 
 /*
- * Runs nreq requests in one kernel launch on `stream`.  Requests of the same
- * generator are grouped, in array order, into one work item that one block
- * runs start to finish (a generator's stream is sequential, Sec. 3.2); work
- * items of different generators run in parallel blocks.  Blocked layout:
+ * Runs nreq requests in one generation launch on `stream`.  Requests of the
+ * same generator are grouped, in array order, into one work item (a
+ * generator's stream is sequential, Sec. 3.2); work items of different
+ * generators run in parallel blocks.  In the blocked layout an item may run as
+ * jump-ahead pieces (mtgp_config.pieces), whose start states one jump launch
+ * computes first; the outputs are the same.  Blocked layout:
  * request j writes elements [out_offset, out_offset + n) of dev_out.
  * Interleaved layout: every request has the same n and a distinct generator,
  * out_offset is ignored, and number k of request j goes to element
  * (k / chunk) * (nreq * chunk) + j * chunk + k % chunk.
  * dev_out must be 4-byte aligned (16-byte aligned for the fastest stores) and
- * large enough; it is caller-owned.  Errors: MTGP_EINVAL (bad index, dtype or
- * layout), MTGP_EBUSY, MTGP_ENOMEM, MTGP_ECUDA.
+ * large enough; it is caller-owned.  A stream being captured into a CUDA
+ * graph is refused, as by every pool call that takes a stream: the work list
+ * is copied from a pool buffer that the next call reuses (mtgp_graph_create
+ * captures a pool launch).  Errors: MTGP_EINVAL (bad index, dtype or layout,
+ * stream under capture), MTGP_EBUSY, MTGP_ENOMEM, MTGP_ECUDA.
  */
 mtgp_status mtgp_pool_generate(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
                                void *dev_out, mtgp_layout layout, void *stream);
@@ -507,7 +511,8 @@ void mtgp_server_destroy(mtgp_server *s);
  * until the process exits.  count > MTGP_NOALLOC_MAX_GENS or
  * nreq > MTGP_NOALLOC_MAX_REQS returns MTGP_EINVAL with a message.  The first
  * call on each device looks up that array's device address (a one-time
- * set-up); make that first call before any stream capture.  Every call
+ * set-up).  The records are copied out of the call's own host memory, so a
+ * stream being captured into a CUDA graph is refused (MTGP_EINVAL).  Every call
  * shares the array and overwrites it (its control words are cleared on each
  * call), so calls that overlap on the GPU -- on different streams, or from
  * several host threads -- race; order them on one stream.  The records are

@@ -249,8 +249,25 @@ mtgp_status pool_sync(mtgp_pool *p)
     return MTGP_OK;
 }
 
+// A pool call copies its work list out of the pool's pinned staging buffer,
+// which the next call overwrites, and records the pool's completion events;
+// captured into a caller's CUDA graph, a replay would read whatever the buffer
+// then holds.  Calls on a stream under capture are therefore refused:
+// mtgp_graph_* is the captured form.
+mtgp_status refuse_capture(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(s, &cap), "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(MTGP_EINVAL, "the stream is being captured into a CUDA graph: pool calls cannot be "
+                                 "captured (mtgp_graph_create captures a pool launch)");
+    return MTGP_OK;
+}
+
 mtgp_status pool_busy_check(mtgp_pool *p, cudaStream_t s)
 {
+    mtgp_status st = refuse_capture(s);
+    if (st != MTGP_OK) return st;
     if (!p->used || s == p->last_stream) return MTGP_OK;
     const cudaError_t e = cudaEventQuery(p->ev_done);
     if (e == cudaErrorNotReady)
@@ -434,11 +451,6 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
 {
     const mtgp_config &c = p->cfg;
     if (c.pieces == 1u || plan->work.empty()) return MTGP_OK;
-    // the annihilators and polynomials may need synchronous GPU work and
-    // copies, which a stream being captured into a graph cannot take
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    CU(cudaStreamIsCapturing(s, &cap), "cudaStreamIsCapturing");
-    if (cap != cudaStreamCaptureStatusNone) return MTGP_OK;
     const uint64_t min_piece = 1ull << (c.piece_log2 ? c.piece_log2 : 20u);
     // auto: pieces of about Lt = total / (16 SMs) numbers, so that the launch
     // has about 16 equal shares of work per SM and long items stop setting its
@@ -725,6 +737,8 @@ mtgp_status mtgp_pool_create(const mtgp_params *ps, const uint32_t *gen_ids, con
             }
         }
         cudaStream_t s = (cudaStream_t)stream;
+        mtgp_status cs = refuse_capture(s);
+        if (cs != MTGP_OK) return cs;
         mtgp_pool *p = new (std::nothrow) mtgp_pool;
         if (!p) return fail(MTGP_ENOMEM, "host allocation");
         p->count = count;
@@ -1018,6 +1032,7 @@ void mtgp_pool_destroy(mtgp_pool *p)
     if (p->ev_done) cudaEventDestroy(p->ev_done);
     if (p->ev_upload) cudaEventDestroy(p->ev_upload);
     delete p;
+    (void)cudaGetLastError();      // the statuses above are ignored: leave none behind
 }
 
 // ---- single generator: a pool of one ---------------------------------------
@@ -1148,7 +1163,9 @@ mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mt
         if (!p || !out || max_items == 0) return fail(MTGP_EINVAL, "graph: NULL pool/out or max_items == 0");
         *out = nullptr;
         cudaStream_t s = (cudaStream_t)stream;
-        mtgp_status st = pool_sync(p);
+        mtgp_status st = refuse_capture(s);
+        if (st != MTGP_OK) return st;
+        st = pool_sync(p);
         if (st != MTGP_OK) return st;
         mtgp_config c = p->cfg;
         c.persistent = 1u;                                   // a fixed grid pulls however many items there are
@@ -1294,6 +1311,7 @@ void mtgp_graph_destroy(mtgp_graph *g)
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     cudaFree(g->d_buf);
     delete g;
+    (void)cudaGetLastError();      // the statuses above are ignored: leave none behind
 }
 
 // ---- error words -----------------------------------------------------------------

@@ -126,6 +126,11 @@ GenKernel flow_kernel_w16(uint32_t cmax);
 // Records msg as the calling thread's last error and returns status.
 int report_error(int status, const char *msg);
 
+// The runtime keeps one last-error word per host thread, and a clean-up call
+// whose status is ignored can leave an error there; the launch wrappers clear
+// it first, so that the check after a launch reports that launch alone.
+inline void clear_stale_error() { (void)cudaGetLastError(); }
+
 bool threads_supported(uint32_t threads, uint32_t form);
 // Smallest compiled QMAX >= nq for this block size and form, 0 if none.
 // In the split and flow forms a thread owns ceil(S / (threads / 2)) columns.

@@ -271,6 +271,7 @@ cudaError_t launch_jump_fused(const DevGen *gens, const uint32_t *src_base, uint
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
+    clear_stale_error();
     k<<<njobs, kFusedThreads, smem, s>>>(gens, src_base, dst_base, jobs, seq_cap, max_N);
     return cudaGetLastError();
 }
@@ -281,6 +282,7 @@ cudaError_t launch_walk(const DevGen *gens, const uint32_t *src_base, uint32_t *
     if (!njobs) return cudaSuccess;
     if (max_N < 3u || max_N > 4096u) return cudaErrorInvalidValue;
     const uint32_t Rb = pow2_at_least(2u * max_N);              // >= N + S for every job
+    clear_stale_error();
     k_walk<<<njobs, kJumpThreads, Rb * sizeof(uint32_t), s>>>(gens, src_base, seq_base, jobs, Rb);
     return cudaGetLastError();
 }
@@ -291,6 +293,7 @@ cudaError_t launch_jump_sum(const DevGen *gens, const uint32_t *seq_base, uint32
     if (!njobs) return cudaSuccess;
     if (max_N < 3u || max_N > 4096u) return cudaErrorInvalidValue;
     const size_t smem = (size_t)max_N * sizeof(uint32_t);
+    clear_stale_error();
     if (max_N <= 8u * kJumpThreads)
         k_jump_sum<8><<<njobs, kJumpThreads, smem, s>>>(gens, seq_base, dst_base, jobs);
     else

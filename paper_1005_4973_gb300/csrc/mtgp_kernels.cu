@@ -107,6 +107,7 @@ cudaError_t launch_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
                         const uint64_t *seeds, uint32_t first, uint32_t count, cudaStream_t s)
 {
     if (count == 0) return cudaSuccess;
+    clear_stale_error();
     k_seed<<<count, 256, 0, s>>>(gens, state, gen_ids, seeds, first);
     return cudaGetLastError();
 }
@@ -126,6 +127,7 @@ cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t form
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
+    clear_stale_error();
     k<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -150,6 +152,7 @@ cudaError_t launch_fill(uint32_t *buf, uint64_t words, uint32_t pattern, cudaStr
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    clear_stale_error();
     k_fill<<<(unsigned)sms * 8u, 512, 0, s>>>(reinterpret_cast<uint4 *>(buf), words / 4u, pattern);
     return cudaGetLastError();
 }

@@ -149,10 +149,17 @@ extern "C" mtgp_status mtgp_generate_noalloc(const mtgp_params *ps, uint32_t cou
     std::memcpy(image.data() + 256u, gens.data(), sizeof(DevGen) * count);
     std::memcpy(image.data() + 256u + gb, work.data(), sizeof(DevWork) * work.size());
     std::memcpy(image.data() + 256u + gb + wb, segs.data(), sizeof(DevSeg) * segs.size());
+    cudaStream_t s = (cudaStream_t)stream;
+    // the records are copied out of this call's own host memory, which is gone
+    // by the time a captured graph would replay the copy: no capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess) return fail_cuda(ce, "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(MTGP_EINVAL, "noalloc: the stream is being captured into a CUDA graph; calls cannot be captured");
     void *base = nullptr;
     mtgp_status st = scratch_address(&base);
     if (st != MTGP_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(base, image.data(), bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail_cuda(e, "noalloc: copy records to scratch");
     unsigned char *b = (unsigned char *)base;

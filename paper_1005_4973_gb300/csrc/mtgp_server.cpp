@@ -365,6 +365,7 @@ void mtgp_server_destroy(mtgp_server *s)
     mtgp_graph_destroy(s->graph);
     cudaFree(s->arena);
     delete s;
+    (void)cudaGetLastError();      // the statuses above are ignored: leave none behind
 }
 
 }  // extern "C"

@@ -255,26 +255,37 @@ def test_autotune_leaves_streams_untouched_and_keeps_parity():
     _check(gens, reqs, as_u32(out), pool)
 
 
-def test_generation_captured_by_the_caller_into_a_cuda_graph():
-    """A pool call made while the caller captures its stream into a CUDA graph
-    is not split (the split needs synchronous work); replaying the graph
-    continues the streams exactly."""
+def test_pool_call_on_a_stream_under_capture_is_refused():
+    """A pool call on a stream that the caller is capturing into a CUDA graph
+    is refused before it touches the stream (its work list would be copied
+    from a buffer that later calls reuse); the pool is unchanged, the next
+    call continues the streams exactly, and no error is left behind for the
+    next launch."""
+    from paper_1005_4973_gb300 import mtgp as L
     gens = _gens([11213, 521])
     pool = lib_pool(gens)
     pool.set_config(pieces=4, piece_log2=10)
     reqs, total = _blocked([(0, 0, 40000), (1, 2, 30000)])
     out = torch.zeros(total, dtype=torch.int32, device="cuda")
     s = torch.cuda.Stream()
-    pool.generate(reqs, out, stream=s)                   # first call: uploads, allocations
+    pool.generate(reqs, out, stream=s)
     s.synchronize()
     first = as_u32(out).copy()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
-        pool.generate(reqs, out, stream=s)
-    g.replay()
-    torch.cuda.synchronize()
+        with pytest.raises(L.MTGPError, match="captur"):
+            pool.generate(reqs, out, stream=s)
+        with pytest.raises(L.MTGPError, match="captur"):
+            pool.jump(0, 1000, stream=s)
+        torch.zeros(4, device="cuda").add_(1)        # keeps the captured graph non-empty
+    assert [pool.position(i) for i in range(2)] == [40000, 30000]
+    pool.generate(reqs, out, stream=s)
+    s.synchronize()
     second = as_u32(out).copy()
     for g_, (dt, n, off) in ((0, (0, 40000, 0)), (1, (2, 30000, 40000))):
         ref, _ = oracle_stream(gens[g_], [(dt, n), (dt, n)])
         assert np.array_equal(first[off:off + n], ref[0])
         assert np.array_equal(second[off:off + n], ref[1])
+    fresh = lib_pool(gens)                           # a launch right after reports itself only
+    fresh.generate(reqs, out)
+    torch.cuda.synchronize()

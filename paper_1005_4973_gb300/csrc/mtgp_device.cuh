@@ -40,7 +40,28 @@ __device__ __forceinline__ uint32_t finish(uint32_t dt, uint32_t o)
 struct GenCtx {
     uint32_t N, M, mask, sh1, sh2, S;
     uint32_t rec_r, tmp_r;      // this lane's table entries rec[lane & 15], tmp[lane & 15]
+    uint32_t tmpf_r;            // 0x3F800000 | (tmp_r >> 9): the single-precision table of Sec. 6
 };
+
+// The tempering table that outputs of dtype DT read: tmp for integers, the
+// pre-shifted single-precision table for floats (Sec. 6), with which a float
+// output is (x >> 9) ^ entry -- the bits of 0x3F800000 | ((x ^ tmp) >> 9),
+// since x >> 9 leaves the nine high bits clear.
+template <int DT>
+__device__ __forceinline__ uint32_t out_table(const GenCtx &g)
+{
+    return DT == 0 ? g.tmp_r : g.tmpf_r;
+}
+
+// Output value of dtype DT from the new word xn and its entry v of out_table<DT>.
+template <int DT>
+__device__ __forceinline__ uint32_t finish_entry(uint32_t xn, uint32_t v)
+{
+    if constexpr (DT == 0) return xn ^ v;
+    const uint32_t f12 = (xn >> 9) ^ v;
+    if constexpr (DT == 1) return f12;
+    return __float_as_uint(__fsub_rn(__uint_as_float(f12), 1.0f));
+}
 
 // Block-wide barrier between rounds; a one-warp block only needs the warp's.
 template <int T>
@@ -80,11 +101,12 @@ __device__ __forceinline__ void round_slots(const GenCtx &g, uint32_t *x, uint32
 #pragma unroll
         for (int q = 0; q < QN; ++q)
             b[q] = __shfl_sync(0xffffffffu, g.rec_r, (int)u[q], 16);
+        const uint32_t tbl = out_table<DT>(g);
 #pragma unroll
         for (int q = 0; q < QN; ++q) {
             uint32_t s = c[q] ^ (c[q] >> 16);
             s ^= s >> 8;
-            c[q] = __shfl_sync(0xffffffffu, g.tmp_r, (int)s, 16);
+            c[q] = __shfl_sync(0xffffffffu, tbl, (int)s, 16);
         }
 #pragma unroll
         for (int q = 0; q < QN; ++q) {
@@ -92,7 +114,7 @@ __device__ __forceinline__ void round_slots(const GenCtx &g, uint32_t *x, uint32
             if (q + 1 < QN || QN < Q || last_lane) {
                 xn_p[q * T] = xn;
                 prev[q] = xn;
-                __stcs(out + q * T, finish(DT, xn ^ c[q]));
+                __stcs(out + q * T, finish_entry<DT>(xn, c[q]));
             }
         }
     }
@@ -130,11 +152,11 @@ __device__ __forceinline__ void round_fast(const GenCtx &g, uint32_t *x, uint32_
         const uint32_t xn = uu ^ __shfl_sync(0xffffffffu, g.rec_r, (int)uu, 16);
         uint32_t s = c0 ^ (c0 >> 16);
         s ^= s >> 8;
-        const uint32_t v = __shfl_sync(0xffffffffu, g.tmp_r, (int)s, 16);
+        const uint32_t v = __shfl_sync(0xffffffffu, out_table<DT>(g), (int)s, 16);
         if (tail_lane) {
             xn_p[q * T] = xn;
             prev[q] = xn;
-            __stcs(out + q * T, finish(DT, xn ^ v));
+            __stcs(out + q * T, finish_entry<DT>(xn, v));
         }
     }
 }
@@ -148,8 +170,28 @@ __device__ __forceinline__ void run_fast(const GenCtx &g, uint32_t *buf, uint32_
     const bool tail_warp = (uint32_t)(Q - 1) * T + (tid & ~31u) < g.S;
     const bool tail_lane = (uint32_t)(Q - 1) * T + tid < g.S;
     out += tid;
-    for (uint32_t r = 0; r < rounds; ++r) {
-        if (rel + g.N + (uint32_t)(Q * T) + 32u > B) {      // compaction: live words to the front
+    const uint32_t span = g.N + (uint32_t)(Q * T) + 32u;   // words a round at rel reads and writes
+    uint32_t r = 0;
+    // Rounds in pairs with one compaction check, when the buffer holds a
+    // second round past the single-round bound: compaction then still finds
+    // rel >= N, so the live words move without overlap.
+    if (B >= g.N + span + g.S) {
+        for (; r + 2u <= rounds; r += 2u) {
+            if (rel + span + g.S > B) {
+                for (uint32_t j = tid; j < g.N; j += T) buf[j] = buf[rel + j];
+                round_sync<T>();
+                rel = 0;
+            }
+            round_fast<T, Q, DT, IL>(g, buf + rel + tid, prev, out, tail_warp, tail_lane);
+            round_sync<T>();
+            round_fast<T, Q, DT, IL>(g, buf + rel + g.S + tid, prev, out + g.S, tail_warp, tail_lane);
+            round_sync<T>();
+            rel += 2u * g.S;
+            out += 2u * g.S;
+        }
+    }
+    for (; r < rounds; ++r) {
+        if (rel + span > B) {                               // compaction: live words to the front
             for (uint32_t j = tid; j < g.N; j += T) buf[j] = buf[rel + j];
             round_sync<T>();
             rel = 0;
@@ -572,6 +614,7 @@ __global__ void __launch_bounds__(2 * RT, (2 * RT) >= 512 ? 1 : 512 / (2 * RT)) 
         g.S = g.N - g.M;
         g.rec_r = gd.rec[lane & 15u];
         g.tmp_r = gd.tmp[lane & 15u];
+        g.tmpf_r = 0x3F800000u | (g.tmp_r >> 9);
         const uint32_t nq = (g.S + RT - 1u) / RT;
         bool ok = nq <= (uint32_t)QMAX && 2u * g.N + nq * RT + 32u <= B;
         if (ok) {
@@ -618,6 +661,7 @@ __global__ void __launch_bounds__(T, QMAX <= 6 ? 512 / T : (T >= 256 ? 1 : 256 /
         g.S = g.N - g.M;
         g.rec_r = gd.rec[lane & 15u];
         g.tmp_r = gd.tmp[lane & 15u];
+        g.tmpf_r = 0x3F800000u | (g.tmp_r >> 9);
         const uint32_t nq = (g.S + T - 1u) / T;
         bool ok = nq <= (uint32_t)QMAX && 2u * g.N + nq * T + 32u <= B;
         if (ok) {
@@ -950,6 +994,7 @@ __global__ void __launch_bounds__(64 * W, (64 * W) >= 512 ? 1 : 512 / (64 * W)) 
         g.S = g.N - g.M;
         g.rec_r = gd.rec[lane & 15u];
         g.tmp_r = gd.tmp[lane & 15u];
+        g.tmpf_r = 0x3F800000u | (g.tmp_r >> 9);
         const uint32_t nc = (g.S + 32u * W - 1u) / (32u * W);          // chunks per recursion warp
         const uint32_t span = 32u * nc;
         bool ok = nc <= (uint32_t)CMAX && 2u * g.N + 2u * g.S + span + 32u <= B;

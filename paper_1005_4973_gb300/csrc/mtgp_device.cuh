@@ -172,22 +172,24 @@ __device__ __forceinline__ void run_fast(const GenCtx &g, uint32_t *buf, uint32_
     out += tid;
     const uint32_t span = g.N + (uint32_t)(Q * T) + 32u;   // words a round at rel reads and writes
     uint32_t r = 0;
-    // Rounds in pairs with one compaction check, when the buffer holds a
-    // second round past the single-round bound: compaction then still finds
+    // Rounds in groups of U with one compaction check, when the buffer holds
+    // U - 1 rounds past the single-round bound: compaction then still finds
     // rel >= N, so the live words move without overlap.
-    if (B >= g.N + span + g.S) {
-        for (; r + 2u <= rounds; r += 2u) {
-            if (rel + span + g.S > B) {
+    constexpr uint32_t U = 2u;        // measured: 3 and 4 lose on short work items
+    if (B >= g.N + span + (U - 1u) * g.S) {
+        for (; r + U <= rounds; r += U) {
+            if (rel + span + (U - 1u) * g.S > B) {
                 for (uint32_t j = tid; j < g.N; j += T) buf[j] = buf[rel + j];
                 round_sync<T>();
                 rel = 0;
             }
-            round_fast<T, Q, DT, IL>(g, buf + rel + tid, prev, out, tail_warp, tail_lane);
-            round_sync<T>();
-            round_fast<T, Q, DT, IL>(g, buf + rel + g.S + tid, prev, out + g.S, tail_warp, tail_lane);
-            round_sync<T>();
-            rel += 2u * g.S;
-            out += 2u * g.S;
+#pragma unroll
+            for (uint32_t k = 0; k < U; ++k) {
+                round_fast<T, Q, DT, IL>(g, buf + rel + k * g.S + tid, prev, out + k * g.S, tail_warp, tail_lane);
+                round_sync<T>();
+            }
+            rel += U * g.S;
+            out += U * g.S;
         }
     }
     for (; r < rounds; ++r) {

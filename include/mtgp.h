@@ -94,12 +94,17 @@ typedef struct mtgp_request {
  * of the `threads` threads owns ceil(S / threads) of the S columns and also
  * tempers and stores them.  Split form: the first half of the block runs the
  * recursion (owning ceil(S / (threads / 2)) columns each) and the second half
- * tempers, converts and stores finished rounds. */
+ * tempers, converts and stores finished rounds.  Wide form: each thread owns
+ * groups of 4 adjacent columns, whose reads overlap (x_{i+1} of one column is
+ * x_i of the next) and whose outputs leave in one 16-byte store; blocked
+ * layouts only (interleaved calls run in the plain form).  On GB300 the plain
+ * form measured fastest; mtgp_autotune tries plain, split and flow. */
 typedef struct mtgp_config {
     uint32_t threads;          /* threads per block: plain 32, 64, 128, 256, 512
                                   (at most 11, 12, 11, 6, 8 columns per thread);
                                   split 128, 256, 512, 1024 (at most 12, 11, 6, 3);
-                                  flow 128, 256, 512, 1024 (at most 12, 11, 6, 8)   */
+                                  flow 128, 256, 512, 1024 (at most 12, 11, 6, 8);
+                                  wide 96, 128, 192 (rounds of at most 1529 words) */
     uint32_t persistent;       /* 1: grid of SMs x blocks_per_sm blocks taking work
                                   items longest first from a device counter;
                                   0: one block per work item                         */
@@ -107,11 +112,13 @@ typedef struct mtgp_config {
     uint32_t chunk;            /* interleaved layout chunk, power of two >= 32       */
     uint32_t buffer_words;     /* shared-memory words per block, 0 = sized from the
                                   launch (>= 2N + owners ceil(S / owners) + 32 is
-                                  required, owners = threads or threads / 2)         */
+                                  required, owners = threads or threads / 2; wide
+                                  form: 4 floor(buffer_words / 4) >= 2N + S + 24)    */
     uint32_t form;             /* 0 plain, 1 split (recursion and output warp groups
                                   handing rounds over through named barriers),
                                   2 flow (split groups, and each recursion warp
-                                  waits only for the warps holding its inputs)       */
+                                  waits only for the warps holding its inputs),
+                                  3 wide (4 adjacent columns per thread)            */
     uint32_t pieces;           /* jump-ahead (Sec. 7): a generator's work in one call
                                   (blocked layout) may run as up to this many pieces
                                   on separate blocks, piece m starting from the state
@@ -310,7 +317,7 @@ mtgp_status mtgp_pool_load(mtgp_pool *p, const void *host_buf, size_t bytes);
 void mtgp_pool_destroy(mtgp_pool *p);
 
 /*
- * Picks the form (plain or split), threads, persistent mode and occupancy
+ * Picks the form (plain, split or flow), threads, persistent mode and occupancy
  * for this pool by timing candidate configurations on `stream` with the given
  * requests written to dev_scratch (caller-owned, large enough for them).  The
  * generators' states are saved before and restored after, so tuning does not

@@ -28,6 +28,8 @@ MAX_SLOTS = {32: 11, 64: 12, 128: 11, 256: 6, 512: 8}
 MAX_SLOTS_SPLIT = {128: 12, 256: 11, 512: 6, 1024: 3}
 # flow form: block size -> chunks of 32 columns per recursion warp (threads / 2 own columns)
 MAX_SLOTS_FLOW = {128: 12, 256: 11, 512: 6, 1024: 8}
+# wide form: block size -> groups of 4 columns per thread
+MAX_SLOTS_WIDE = {96: 4, 128: 3, 192: 2}
 STATUS_NAMES = {0: "MTGP_OK", 1: "MTGP_EINVAL", 2: "MTGP_ENOMEM", 3: "MTGP_ECUDA",
                 4: "MTGP_ETIMEOUT", 5: "MTGP_EBUSY"}
 

@@ -200,6 +200,7 @@ struct mtgp_graph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint32_t B = 0;
+    uint32_t form = 0;                       // form of the captured kernel (3: blocked layouts only)
 };
 
 namespace {
@@ -210,7 +211,7 @@ constexpr uint64_t kSeqCap = 256ull << 20;           // walk scratch words per l
 
 mtgp_status check_config(const mtgp_config &c)
 {
-    if (c.form > 2u) return fail(MTGP_EINVAL, "form must be 0 (plain), 1 (split) or 2 (flow)");
+    if (c.form > 3u) return fail(MTGP_EINVAL, "form must be 0 (plain), 1 (split), 2 (flow) or 3 (wide)");
     if (!threads_supported(c.threads, c.form))
         return fail(MTGP_EINVAL, "no kernel of form %u with %u threads per block", c.form, c.threads);
     if (c.persistent > 1u) return fail(MTGP_EINVAL, "persistent must be 0 or 1");
@@ -376,6 +377,43 @@ mtgp_status build_plan(const mtgp_pool *p, const mtgp_request *reqs, uint32_t nr
 // Kernel shape for a launch running the generators gens[0 .. n): slot count
 // qmax and shared buffer words B under configuration c (items = work items
 // expected, which sets how many blocks per SM the buffer is sized for).
+// Wide form: a round of S words spans at most (S + 6) / 4 + 1 groups of 4
+// columns, QW = ceil(groups / threads) per thread.  The buffer is four
+// sub-buffers of P words with P = 8 mod 32 (stride-1 copies stay free of bank
+// conflicts), at least 2N + S + 24 words in all.
+mtgp_status launch_shape_wide(const mtgp_pool *p, const mtgp_config &c, const uint32_t *gens, size_t n,
+                              size_t items, uint32_t nmax, uint32_t smax, uint32_t *qmax_out, uint32_t *B_out)
+{
+    const uint32_t groups = (smax + 6u) / 4u + 1u;
+    const uint32_t qmax = kernel_slots(c.threads, 3u, (groups + c.threads - 1u) / c.threads);
+    if (!qmax)
+        return fail(MTGP_EINVAL, "no compiled wide kernel runs rounds of %u words with %u threads", smax, c.threads);
+    uint32_t need = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const DevGen &g = p->host_gens[gens[i]];
+        need = std::max(need, 2u * g.N + (g.N - g.M) + 24u);
+    }
+    uint32_t B = c.buffer_words;
+    if (!B) {
+        uint32_t per_sm = c.persistent ? (c.blocks_per_sm ? c.blocks_per_sm : 10u)
+                                       : (uint32_t)std::min<size_t>(12, (items + p->sm_count - 1) / (size_t)p->sm_count);
+        per_sm = std::max(per_sm, 1u);
+        const uint32_t budget = std::min(57344u, (uint32_t)((227u * 1024u / per_sm - 1024u) / 4u));
+        B = std::min(2u * nmax + 32u * smax + 32u, budget);
+        B = std::max(B, need);
+        uint32_t P = B / 4u;
+        P = P < 8u ? 8u : ((P - 8u) & ~31u) + 8u;                 // 8 mod 32, not above B / 4
+        if (4u * P < need) P += 32u;
+        B = 4u * P;
+    }
+    if (B / 4u * 4u < need)
+        return fail(MTGP_EINVAL, "buffer_words %u below the minimum %u for this launch", B, (need + 3u) & ~3u);
+    if (B > 57344u) return fail(MTGP_EINVAL, "state too large for shared memory (%u words)", B);
+    *qmax_out = qmax;
+    *B_out = B;
+    return MTGP_OK;
+}
+
 mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_t *gens, size_t n, size_t items,
                          uint32_t *qmax_out, uint32_t *B_out)
 {
@@ -385,6 +423,7 @@ mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_
         nmax = std::max(nmax, g.N);
         smax = std::max(smax, g.N - g.M);
     }
+    if (c.form == 3u) return launch_shape_wide(p, c, gens, n, items, nmax, smax, qmax_out, B_out);
     const uint32_t owners = c.form ? c.threads / 2u : c.threads;   // threads owning columns
     const uint32_t qmax = kernel_slots(c.threads, c.form, (smax + owners - 1u) / owners);
     if (!qmax)
@@ -576,7 +615,14 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
 mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStream_t s)
 {
     if (plan.work.empty()) return MTGP_OK;
-    const mtgp_config &c = p->cfg;
+    mtgp_config c = p->cfg;
+    if (c.form == 3u)   // the wide form writes blocked segments only: interleaved launches run plain
+        for (const DevSeg &sg : plan.segs)
+            if (sg.chunk_log2 != kBlocked) {
+                c.form = 0u;
+                c.threads = 128u;
+                break;
+            }
     std::vector<uint32_t> gens(plan.work.size());
     for (size_t i = 0; i < plan.work.size(); ++i) gens[i] = plan.work[i].gen;
     uint32_t qmax = 0, B = 0;
@@ -1113,7 +1159,7 @@ mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
         const mtgp_config orig = p->cfg;
         std::vector<mtgp_config> cands;
         for (uint32_t pieces : {0u, 1u})                     // jump-ahead pieces: auto, or none
-            for (uint32_t form : {0u, 1u, 2u})
+            for (uint32_t form : {0u, 1u, 2u})             // the wide form (3) measured slower everywhere
                 for (uint32_t threads : {32u, 64u, 128u, 256u, 512u, 1024u})
                     for (uint32_t pers : {0u, 1u})
                         for (uint32_t bps : {0u, 1u, 2u, 3u, 4u, 6u, 8u}) {
@@ -1184,6 +1230,7 @@ mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mt
         g->pool = p;
         g->max_items = max_items;
         g->B = B;
+        g->form = c.form;
         g->d_bytes = 256u + (size_t)max_items * (sizeof(DevWork) + sizeof(DevSeg));
         auto bail = [&](mtgp_status r) { mtgp_graph_destroy(g); return r; };
         cudaError_t e;
@@ -1247,6 +1294,8 @@ mtgp_status mtgp_graph_set_requests(mtgp_graph *g, const mtgp_request *reqs, uin
                         plan.segs.size(), g->max_items);
         if (plan.total && !dev_out) return fail(MTGP_EINVAL, "dev_out is NULL");
         if (((uintptr_t)dev_out & 3u) != 0) return fail(MTGP_EINVAL, "dev_out must be 4-byte aligned");
+        if (g->form == 3u && layout != MTGP_LAYOUT_BLOCKED)
+            return fail(MTGP_EINVAL, "graph: the wide form (3) it captured writes blocked layouts only");
         const int k = g->slot;
         if (g->stage_used[k]) CU(cudaEventSynchronize(g->ev_stage[k]), "cudaEventSynchronize");
         char *h = (char *)g->h_stage[k];

@@ -117,6 +117,10 @@ GenKernel split_kernel_rt64(uint32_t qmax);
 GenKernel split_kernel_rt128(uint32_t qmax);
 GenKernel split_kernel_rt256(uint32_t qmax);
 GenKernel split_kernel_rt512(uint32_t qmax);
+// Wide-form kernels (form 3): T threads per block, each owning QW groups of 4
+// adjacent columns of a round; T in {96, 128, 192}, QW in {1, 2, 4},
+// {1, 2, 3}, {1, 2}.  Blocked layouts only.
+GenKernel wide_kernel(uint32_t threads, uint32_t qw);
 // Flow-form kernels: blocks of 2 W warps (W recursion + W output warps).
 GenKernel flow_kernel_w2(uint32_t cmax);
 GenKernel flow_kernel_w4(uint32_t cmax);

@@ -57,6 +57,7 @@ GenKernel pick(uint32_t threads, uint32_t form, uint32_t qmax, bool interleave =
         GenKernel k = gen_kernel_t128_il(qmax);
         if (k) return k;
     }
+    if (form == 3u) return wide_kernel(threads, qmax);
     if (form == 2u) {
         switch (threads) {
         case 128: return flow_kernel_w2(qmax);
@@ -87,18 +88,30 @@ GenKernel pick(uint32_t threads, uint32_t form, uint32_t qmax, bool interleave =
 
 }  // namespace
 
+// Slot counts compiled: MTGP_QMAX_LIST for forms 0-2, 1..4 groups for form 3.
+static const uint32_t kSlots[] = {MTGP_QMAX_LIST};
+static const uint32_t kWideSlots[] = {1, 2, 3, 4};
+
 bool threads_supported(uint32_t threads, uint32_t form)
 {
-    static const uint32_t compiled[] = {MTGP_QMAX_LIST};
-    for (uint32_t q : compiled)
+    if (form == 3u) {
+        for (uint32_t q : kWideSlots)
+            if (pick(threads, form, q)) return true;
+        return false;
+    }
+    for (uint32_t q : kSlots)
         if (pick(threads, form, q)) return true;
     return false;
 }
 
 uint32_t kernel_slots(uint32_t threads, uint32_t form, uint32_t nq)
 {
-    static const uint32_t compiled[] = {MTGP_QMAX_LIST};
-    for (uint32_t q : compiled)
+    if (form == 3u) {
+        for (uint32_t q : kWideSlots)
+            if (q >= nq && pick(threads, form, q)) return q;
+        return 0;
+    }
+    for (uint32_t q : kSlots)
         if (q >= nq && pick(threads, form, q)) return q;
     return 0;
 }

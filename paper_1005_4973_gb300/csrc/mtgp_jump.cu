@@ -132,17 +132,59 @@ __global__ void __launch_bounds__(kJumpThreads) k_jump_sum(const DevGen *gens, c
 // slides a 2R-word window along the sequence: for each R coefficients it
 // loads the next R words (R = 12: three 16-byte loads at a 48-byte lane
 // stride, which touch every bank exactly once per 8 lanes).
+// XORs into acc the windows starting at words U0 + b of (lo, hi) for the set
+// bits b of MASK (the compiler folds the chain into 3-input XORs).
+template <int R, int U0, int MASK>
+__device__ __forceinline__ void xor_windows(uint32_t (&acc)[R], const uint32_t (&lo)[R], const uint32_t (&hi)[R])
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        uint32_t t = acc[r];
+        if constexpr ((MASK & 1) != 0) t ^= (U0 + r < R) ? lo[U0 + r] : hi[U0 + r - R];
+        if constexpr ((MASK & 2) != 0) t ^= (U0 + 1 + r < R) ? lo[U0 + 1 + r] : hi[U0 + 1 + r - R];
+        if constexpr ((MASK & 4) != 0) t ^= (U0 + 2 + r < R) ? lo[U0 + 2 + r] : hi[U0 + 2 + r - R];
+        if constexpr ((MASK & 8) != 0) t ^= (U0 + 3 + r < R) ? lo[U0 + 3 + r] : hi[U0 + 3 + r - R];
+        acc[r] = t;
+    }
+}
+
+// The four coefficients U0 .. U0+3 of a group, one warp-uniform branch for
+// all sixteen patterns.
+template <int R, int U0>
+__device__ __forceinline__ void sum_nibble(uint32_t (&acc)[R], const uint32_t (&lo)[R], const uint32_t (&hi)[R],
+                                           uint32_t nib)
+{
+    switch (nib) {
+    case 1: xor_windows<R, U0, 1>(acc, lo, hi); break;
+    case 2: xor_windows<R, U0, 2>(acc, lo, hi); break;
+    case 3: xor_windows<R, U0, 3>(acc, lo, hi); break;
+    case 4: xor_windows<R, U0, 4>(acc, lo, hi); break;
+    case 5: xor_windows<R, U0, 5>(acc, lo, hi); break;
+    case 6: xor_windows<R, U0, 6>(acc, lo, hi); break;
+    case 7: xor_windows<R, U0, 7>(acc, lo, hi); break;
+    case 8: xor_windows<R, U0, 8>(acc, lo, hi); break;
+    case 9: xor_windows<R, U0, 9>(acc, lo, hi); break;
+    case 10: xor_windows<R, U0, 10>(acc, lo, hi); break;
+    case 11: xor_windows<R, U0, 11>(acc, lo, hi); break;
+    case 12: xor_windows<R, U0, 12>(acc, lo, hi); break;
+    case 13: xor_windows<R, U0, 13>(acc, lo, hi); break;
+    case 14: xor_windows<R, U0, 14>(acc, lo, hi); break;
+    case 15: xor_windows<R, U0, 15>(acc, lo, hi); break;
+    default: break;
+    }
+}
+
+// The R coefficients of a group (bits of cb) applied to the sliding window
+// (lo, hi): coefficient u selects the words u .. u + R - 1.
 template <int R, int T>
 __device__ __forceinline__ void sum_group(uint32_t (&acc)[R], const uint32_t (&lo)[R], const uint32_t (&hi)[R],
                                           uint32_t cb)
 {
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-        if ((cb >> u) & 1u) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] ^= (u + r < R) ? lo[u + r] : hi[u + r - R];
-        }
-    }
+    static_assert(R % 4 == 0, "coefficients go in nibbles");
+    sum_nibble<R, 0>(acc, lo, hi, cb & 15u);
+    if constexpr (R > 4) sum_nibble<R, 4>(acc, lo, hi, (cb >> 4) & 15u);
+    if constexpr (R > 8) sum_nibble<R, 8>(acc, lo, hi, (cb >> 8) & 15u);
+    if constexpr (R > 12) sum_nibble<R, 12>(acc, lo, hi, (cb >> 12) & 15u);
 }
 
 template <int R>

@@ -498,7 +498,11 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
     const uint64_t Lt = c.pieces ? 0u : (plan->total + 16ull * (uint64_t)std::max(p->sm_count, 1) - 1u) /
                                            (16ull * (uint64_t)std::max(p->sm_count, 1));
     if (kt < 2u) return MTGP_OK;
-    const bool few = plan->work.size() < (size_t)std::max(p->sm_count, 1);
+    const uint64_t sms = (uint64_t)std::max(p->sm_count, 1);
+    const bool few = plan->work.size() < sms;
+    // auto, fewer items than SMs: at most 1 + 2 SMs / items pieces per item, so
+    // that the jumps run in one wave (two jump blocks fit on an SM)
+    const uint64_t kfew = 1u + 2u * sms / (uint64_t)plan->work.size();
     struct Cut {
         uint32_t k;
         uint64_t L;
@@ -512,10 +516,11 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
         const DevGen &g = p->host_gens[dw.gen];
         // auto: a piece at least mexp N / 4 numbers long, so that its jump
         // (about 0.7 mexp N word operations) stays a few per cent of its work;
-        // when the work items do not fill the SMs, pieces down to mexp N / 32
-        // (jumps then run on SMs that would otherwise idle)
+        // when the work items do not fill the SMs, pieces down to 2^14 numbers
+        // (jumps then run on SMs that would otherwise idle, and a launch's time
+        // is one jump plus one piece)
         const uint64_t lmin = c.piece_log2 ? min_piece
-                              : few ? std::max<uint64_t>(1u << 14, (uint64_t)g.mexp * g.N / 32u)
+                              : few ? (uint64_t)1u << 14
                                     : std::max<uint64_t>(min_piece, (uint64_t)g.mexp * g.N / 4u);
         if (dw.total < 2u * lmin) continue;
         bool blocked = true;
@@ -524,6 +529,7 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
         if (!blocked) continue;
         uint64_t k = std::min<uint64_t>(kt, dw.total / lmin);
         if (Lt) k = std::min<uint64_t>(k, (dw.total + Lt - 1u) / Lt);
+        if (!c.pieces && few) k = std::min<uint64_t>(k, kfew);
         if (k < 2u) continue;
         uint64_t L = (dw.total + k - 1u) / k;
         L = (L + 63u) & ~63ull;

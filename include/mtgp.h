@@ -105,10 +105,13 @@ typedef struct mtgp_config {
                                   split 128, 256, 512, 1024 (at most 12, 11, 6, 3);
                                   flow 128, 256, 512, 1024 (at most 12, 11, 6, 8);
                                   wide 96, 128, 192 (rounds of at most 1529 words) */
-    uint32_t persistent;       /* 1: grid of SMs x blocks_per_sm blocks taking work
-                                  items longest first from a device counter;
-                                  0: one block per work item                         */
-    uint32_t blocks_per_sm;    /* persistent grid occupancy, 0 = what fits            */
+    uint32_t persistent;       /* 1 (default): grid of SMs x blocks_per_sm blocks
+                                  taking work items longest first from a device
+                                  counter; 0: one block per work item               */
+    uint32_t blocks_per_sm;    /* persistent grid occupancy; 0 = what the kernel's
+                                  registers allow, shared buffers sized for it, and
+                                  a launch whose items all fit at once runs one
+                                  block per item                                    */
     uint32_t chunk;            /* interleaved layout chunk, power of two >= 32       */
     uint32_t buffer_words;     /* shared-memory words per block, 0 = sized from the
                                   launch (>= 2N + owners ceil(S / owners) + 32 is

@@ -205,7 +205,7 @@ struct mtgp_graph {
 
 namespace {
 
-const mtgp_config kDefaultConfig = {128u, 0u, 0u, 256u, 0u, 0u, 0u, 0u};
+const mtgp_config kDefaultConfig = {128u, 1u, 0u, 256u, 0u, 0u, 0u, 0u};   // plain, persistent, auto
 constexpr size_t kJumpStoreCap = (size_t)1 << 30;   // device bytes of cached jump polynomials
 constexpr uint64_t kSeqCap = 256ull << 20;           // walk scratch words per launch
 
@@ -442,8 +442,15 @@ mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_
     }
     uint32_t B = c.buffer_words;
     if (!B) {
-        uint32_t per_sm = c.persistent ? (c.blocks_per_sm ? c.blocks_per_sm : 6u)
+        uint32_t per_sm = c.persistent ? c.blocks_per_sm
                                        : (uint32_t)std::min<size_t>(8, (items + p->sm_count - 1) / (size_t)p->sm_count);
+        if (c.persistent && !per_sm) {
+            // as many blocks as the kernel's registers and threads allow, with
+            // buffers sized for them (measured: C2 +1 %, C3 and C4 level)
+            int occ = 0;
+            if (generate_occupancy(c.threads, c.form, qmax, need, &occ) != cudaSuccess || occ < 1) occ = 6;
+            per_sm = (uint32_t)occ;
+        }
         per_sm = std::max(per_sm, 1u);
         const uint32_t budget = std::min(57344u, (uint32_t)((227u * 1024u / per_sm - 1024u) / 4u));
         B = std::min(2u * nmax + 32u * smax + 32u, budget);
@@ -670,13 +677,19 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     // fewer work items than SMs: each block's round latency is the time, so
     // the kernel with interleaved round tails (where compiled)
     const bool interleave = plan.work.size() < (size_t)std::max(p->sm_count, 1);
-    if (c.persistent) {
-        CU(cudaMemsetAsync(p->d_ctl, 0, sizeof(unsigned), s), "reset work counter");
+    bool persistent = c.persistent != 0u;
+    if (persistent) {
         int occ = 0;
         CU(generate_occupancy(c.threads, c.form, qmax, B, &occ, interleave), "occupancy");
         if (occ < 1) return fail(MTGP_EINVAL, "configuration does not fit on an SM");
         const int per_sm = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, occ) : occ;
-        grid = std::min<uint32_t>(grid, (uint32_t)(per_sm * p->sm_count));
+        // every item resident at once: one block per item, no work counter
+        if (!c.blocks_per_sm && plan.work.size() <= (size_t)per_sm * (size_t)p->sm_count)
+            persistent = false;
+        else {
+            CU(cudaMemsetAsync(p->d_ctl, 0, sizeof(unsigned), s), "reset work counter");
+            grid = std::min<uint32_t>(grid, (uint32_t)(per_sm * p->sm_count));
+        }
     }
     LaunchArgs a{};
     a.gens = p->d_gens;
@@ -688,7 +701,7 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     a.err = p->d_ctl + 1;
     a.nwork = (uint32_t)plan.work.size();
     a.buf_words = B;
-    a.persistent = c.persistent;
+    a.persistent = persistent ? 1u : 0u;
     a.jstate = p->d_jstate;
     a.interleave = interleave ? 1u : 0u;
     CU(launch_generate(a, c.threads, c.form, qmax, grid, s), "generate kernel launch");

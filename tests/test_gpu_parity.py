@@ -118,7 +118,11 @@ def test_launch_shapes(form, persistent):
         for k, n in enumerate(RAGGED[g % 3::3] + [RAGGED[(g + 1) % len(RAGGED)]]):
             reqs.append((g, (g + k) % 3, n, off))
             off += n
-    pool, out = _run(gens, reqs, config=dict(threads=threads, form=fm, persistent=persistent))
+    # persistent: one block per SM, so that the blocks pull several items from
+    # the work counter (with blocks_per_sm = 0 a launch whose items fit in one
+    # wave runs one block per item)
+    cfg = dict(threads=threads, form=fm, persistent=persistent, blocks_per_sm=persistent)
+    pool, out = _run(gens, reqs, config=cfg)
     _check_blocked(gens, reqs, out, pool)
 
 

@@ -70,7 +70,7 @@ def _ragged_requests(ngens, seed):
 def test_ragged_segments_every_residue(threads, persistent):
     gens = [g for g in MIXED if _fits(g, threads)]
     pool = lib_pool(gens)
-    pool.set_config(threads=threads, form=3, persistent=persistent)
+    pool.set_config(threads=threads, form=3, persistent=persistent, blocks_per_sm=persistent)
     reqs, total = _ragged_requests(len(gens), 17 + threads + persistent)
     out = torch.full((total + 8,), 0x5A, dtype=torch.int32, device="cuda")
     pool.generate(reqs, out)

@@ -81,3 +81,27 @@ def test_noalloc_rejects_calls_beyond_its_scratch():
     reqs = [(0, 0, 1, k) for k in range(L.MTGP_NOALLOC_MAX_REQS + 1)]
     st = _noalloc(L, ps[:1], states, [0], reqs, out, torch.cuda.current_stream().cuda_stream)
     assert st == L.MTGP_EINVAL and "scratch limit" in L.last_error()
+
+
+def test_noalloc_refuses_a_stream_under_capture():
+    # the records are copied out of the call's own host memory, so a captured
+    # copy would replay from memory that is gone: the call is refused before it
+    # touches the stream, and the next call on that stream runs normally
+    M, L = _lib()
+    p = M.mtgp_params_draw(11213, 1, 0)
+    pool = M.Pool([p], [0], [1234])
+    states = torch.zeros(352, dtype=torch.int32, device="cuda")
+    states[:p.N] = torch.from_numpy(pool.read_state(0).view(np.int32)).cuda()
+    out = torch.zeros(4096, dtype=torch.int32, device="cuda")
+    ref = torch.zeros(4096, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        st = _noalloc(L, [p], states, [0], [(0, 0, 4096, 0)], out, s.cuda_stream)
+        torch.zeros(4, device="cuda").add_(1)        # keeps the captured graph non-empty
+    assert st == L.MTGP_EINVAL and "captur" in L.last_error()
+    assert _noalloc(L, [p], states, [0], [(0, 0, 4096, 0)], out, s.cuda_stream) == L.MTGP_OK
+    pool.generate([(0, 0, 4096, 0)], ref)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    pool.close()

@@ -1,6 +1,7 @@
 // Host side of libmtgp: parameter sets, device-resident generator pools, work
 // lists and launches.  Implements the C ABI declared in include/mtgp.h.
 #include "mtgp.h"
+#include "mtgp_graph.h"
 #include "mtgp_internal.h"
 #include "mtgp_jump.h"
 
@@ -201,6 +202,13 @@ struct mtgp_graph {
     cudaGraphExec_t exec = nullptr;
     uint32_t B = 0;
     uint32_t form = 0;                       // form of the captured kernel (3: blocked layouts only)
+    // jump-ahead pieces (Sec. 7): the capture holds a jump launch over up to
+    // max_items jobs before the generation launch, writing the pieces' start
+    // states to d_jstate
+    bool jump = false;
+    uint32_t *d_jstate = nullptr;
+    uint64_t jstate_cap = 0;                 // words
+    uint32_t j_max_N = 0, j_max_nseq = 0, j_max_ncoef = 0;
 };
 
 namespace {
@@ -1221,8 +1229,24 @@ mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
     });
 }
 
+}  // extern "C"
+
 // ---- graph-captured batched launch -------------------------------------------
-mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mtgp_graph **out)
+namespace {
+
+// Device buffer of a graph: control words [0, 256) (work counter, error word,
+// item count at 8, output base at 16, job count at 24), then max_items work
+// items, max_items segments and, with pieces, max_items jump jobs.
+size_t graph_job_offset(uint32_t max_items)
+{
+    return 256u + (size_t)max_items * (sizeof(DevWork) + sizeof(DevSeg));
+}
+
+}  // namespace
+
+// The graph of mtgp_graph_create; allow_pieces = false keeps every work item
+// whole (the server: its generators' annihilating polynomials are not known).
+mtgp_status mtgp::graph_create(mtgp_pool *p, uint32_t max_items, void *stream, bool allow_pieces, mtgp_graph **out)
 {
     return guarded([&]() -> mtgp_status {
         if (!p || !out || max_items == 0) return fail(MTGP_EINVAL, "graph: NULL pool/out or max_items == 0");
@@ -1250,7 +1274,17 @@ mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mt
         g->max_items = max_items;
         g->B = B;
         g->form = c.form;
-        g->d_bytes = 256u + (size_t)max_items * (sizeof(DevWork) + sizeof(DevSeg));
+        // pieces when the pool's configuration allows them and every generator's
+        // jump fits the fused kernel (polynomials of degree up to mexp)
+        g->jump = allow_pieces && c.pieces != 1u;
+        for (uint32_t i = 0; g->jump && i < p->count; ++i) {
+            const DevGen &hg = p->host_gens[i];
+            g->j_max_N = std::max(g->j_max_N, hg.N);
+            g->j_max_ncoef = std::max(g->j_max_ncoef, hg.mexp + 1u);
+            g->j_max_nseq = std::max(g->j_max_nseq, jump_seq_words(hg.N, hg.mexp + 1u));
+        }
+        if (g->jump) g->jump = jump_fused_fits(g->j_max_N, g->j_max_nseq, g->j_max_ncoef);
+        g->d_bytes = graph_job_offset(max_items) + (g->jump ? (size_t)max_items * sizeof(DevJump) : 0u);
         auto bail = [&](mtgp_status r) { mtgp_graph_destroy(g); return r; };
         cudaError_t e;
     #define CUG(call, what)                                       \
@@ -1259,6 +1293,11 @@ mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mt
             if (e != cudaSuccess) return bail(cuda_fail(e, what)); \
         } while (0)
         CUG(cudaMalloc(&g->d_buf, g->d_bytes), "cudaMalloc graph work list");
+        if (g->jump) {
+            g->jstate_cap = (uint64_t)max_items * ((g->j_max_N + 3u) & ~3u);
+            CUG(cudaMalloc(&g->d_jstate, 4u * g->jstate_cap), "cudaMalloc graph piece states");
+            CUG(prepare_jump_fused(g->j_max_N, g->j_max_nseq, g->j_max_ncoef), "jump kernel shared memory");
+        }
         CUG(cudaMemsetAsync(g->d_buf, 0, 256u, s), "cudaMemsetAsync");
         for (int k = 0; k < 2; ++k) {
             CUG(cudaHostAlloc(&g->h_stage[k], g->d_bytes, cudaHostAllocDefault), "cudaHostAlloc");
@@ -1280,8 +1319,14 @@ mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mt
         a.out_dev = (uint32_t *const *)(b + 16u);
         a.buf_words = B;
         a.persistent = 1u;
+        a.jstate = g->d_jstate;
         CUG(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
         cudaError_t e1 = cudaMemsetAsync(b, 0, sizeof(unsigned), g->cap_stream);
+        if (e1 == cudaSuccess && g->jump)
+            e1 = launch_jump_fused(p->d_gens, p->d_state, g->d_jstate,
+                                   (const DevJump *)(b + graph_job_offset(max_items)), max_items, g->j_max_N,
+                                   g->j_max_nseq, g->j_max_ncoef, g->cap_stream, (const uint32_t *)(b + 24u),
+                                   2u * (uint32_t)std::max(p->sm_count, 1));   // two blocks fit on an SM
         cudaError_t e2 = e1 == cudaSuccess ? launch_generate(a, c.threads, c.form, qmax, grid, g->cap_stream) : e1;
         e = cudaStreamEndCapture(g->cap_stream, &g->graph);
         if (e2 != cudaSuccess) return bail(cuda_fail(e2, "graph: capture of the generation launch"));
@@ -1293,6 +1338,13 @@ mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mt
     });
 }
 
+extern "C" {
+
+mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mtgp_graph **out)
+{
+    return mtgp::graph_create(p, max_items, stream, true, out);
+}
+
 mtgp_status mtgp_graph_set_requests(mtgp_graph *g, const mtgp_request *reqs, uint32_t nreq, void *dev_out,
                                     mtgp_layout layout, void *stream)
 {
@@ -1302,29 +1354,55 @@ mtgp_status mtgp_graph_set_requests(mtgp_graph *g, const mtgp_request *reqs, uin
         cudaStream_t s = (cudaStream_t)stream;
         mtgp_status st = pool_busy_check(p, s);
         if (st != MTGP_OK) return st;
+        if (((uintptr_t)dev_out & 3u) != 0) return fail(MTGP_EINVAL, "dev_out must be 4-byte aligned");
+        if (g->form == 3u && layout != MTGP_LAYOUT_BLOCKED)
+            return fail(MTGP_EINVAL, "graph: the wide form (3) it captured writes blocked layouts only");
         const mtgp_config saved = p->cfg;
         p->cfg.persistent = 1u;                              // longest-first order for the fixed grid
         Plan plan;
         st = build_plan(p, reqs, nreq, layout, &plan);
+        bool split = false;
+        if (st == MTGP_OK && g->jump) {
+            // pieces (Sec. 7) as in a pool call, when they fit the captured
+            // capacity and the captured jump kernel; otherwise whole items
+            Plan pieces = plan;
+            split = true;
+            st = split_plan(p, &pieces, s);
+            const bool fits = pieces.work.size() <= g->max_items && pieces.segs.size() <= g->max_items &&
+                              pieces.jobs.size() <= g->max_items && pieces.jstate_words <= g->jstate_cap &&
+                              pieces.jmax_N <= g->j_max_N && pieces.jmax_nseq <= g->j_max_nseq &&
+                              pieces.jmax_ncoef <= g->j_max_ncoef;
+            if (st == MTGP_OK && fits) plan = std::move(pieces);
+        }
         p->cfg = saved;
-        if (st != MTGP_OK) return st;
+        // the work list in place refers to jump polynomials that planning may
+        // have evicted from the cache: replays do nothing until a new list is in
+        auto invalidate = [&](mtgp_status r) {
+            if (split) {
+                (void)cudaMemsetAsync((char *)g->d_buf + 8u, 0, sizeof(uint32_t), s);
+                (void)cudaMemsetAsync((char *)g->d_buf + 24u, 0, sizeof(uint32_t), s);
+            }
+            return r;
+        };
+        if (st != MTGP_OK) return invalidate(st);
         if (plan.work.size() > g->max_items || plan.segs.size() > g->max_items)
-            return fail(MTGP_EINVAL, "graph: %zu work items / %zu segments exceed its capacity %u", plan.work.size(),
-                        plan.segs.size(), g->max_items);
-        if (plan.total && !dev_out) return fail(MTGP_EINVAL, "dev_out is NULL");
-        if (((uintptr_t)dev_out & 3u) != 0) return fail(MTGP_EINVAL, "dev_out must be 4-byte aligned");
-        if (g->form == 3u && layout != MTGP_LAYOUT_BLOCKED)
-            return fail(MTGP_EINVAL, "graph: the wide form (3) it captured writes blocked layouts only");
+            return invalidate(fail(MTGP_EINVAL, "graph: %zu work items / %zu segments exceed its capacity %u",
+                                   plan.work.size(), plan.segs.size(), g->max_items));
+        if (plan.total && !dev_out) return invalidate(fail(MTGP_EINVAL, "dev_out is NULL"));
         const int k = g->slot;
         if (g->stage_used[k]) CU(cudaEventSynchronize(g->ev_stage[k]), "cudaEventSynchronize");
         char *h = (char *)g->h_stage[k];
-        const uint32_t nwork = (uint32_t)plan.work.size();
+        const uint32_t nwork = (uint32_t)plan.work.size(), njobs = (uint32_t)plan.jobs.size();
+        std::memset(h, 0, 256u);
         std::memcpy(h + 8u, &nwork, sizeof nwork);
         std::memcpy(h + 16u, &dev_out, sizeof dev_out);
+        std::memcpy(h + 24u, &njobs, sizeof njobs);
         std::memcpy(h + 256u, plan.work.data(), plan.work.size() * sizeof(DevWork));
         const size_t seg_off = 256u + (size_t)g->max_items * sizeof(DevWork);
         std::memcpy(h + seg_off, plan.segs.data(), plan.segs.size() * sizeof(DevSeg));
-        // control words from [8, 24), then the work items, then the segments
+        const size_t job_off = graph_job_offset(g->max_items);
+        if (njobs) std::memcpy(h + job_off, plan.jobs.data(), plan.jobs.size() * sizeof(DevJump));
+        // control words from [8, 256), then the work items, the segments, the jobs
         CU(cudaMemcpyAsync((char *)g->d_buf + 8u, h + 8u, 248u + plan.work.size() * sizeof(DevWork),
                            cudaMemcpyHostToDevice, s),
            "graph: upload work list");
@@ -1332,6 +1410,10 @@ mtgp_status mtgp_graph_set_requests(mtgp_graph *g, const mtgp_request *reqs, uin
             CU(cudaMemcpyAsync((char *)g->d_buf + seg_off, h + seg_off, plan.segs.size() * sizeof(DevSeg),
                                cudaMemcpyHostToDevice, s),
                "graph: upload segments");
+        if (njobs)
+            CU(cudaMemcpyAsync((char *)g->d_buf + job_off, h + job_off, plan.jobs.size() * sizeof(DevJump),
+                               cudaMemcpyHostToDevice, s),
+               "graph: upload jump jobs");
         CU(cudaEventRecord(g->ev_stage[k], s), "cudaEventRecord");
         g->stage_used[k] = true;
         g->slot ^= 1;
@@ -1349,6 +1431,7 @@ mtgp_status mtgp_graph_launch(mtgp_graph *g, void *stream)
     mtgp_status st = pool_busy_check(g->pool, s);
     if (st != MTGP_OK) return st;
     CU(cudaGraphLaunch(g->exec, s), "cudaGraphLaunch");
+    g->pool->launches += g->jump ? 2u : 1u;                 // jump (whatever its job count) and generation
     CU(cudaEventRecord(g->pool->ev_done, s), "cudaEventRecord");
     g->pool->last_stream = s;
     g->pool->used = true;
@@ -1378,6 +1461,7 @@ void mtgp_graph_destroy(mtgp_graph *g)
     if (g->graph) cudaGraphDestroy(g->graph);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     cudaFree(g->d_buf);
+    cudaFree(g->d_jstate);
     delete g;
     (void)cudaGetLastError();      // the statuses above are ignored: leave none behind
 }

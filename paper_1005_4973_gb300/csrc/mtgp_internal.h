@@ -88,8 +88,14 @@ cudaError_t launch_walk(const DevGen *gens, const uint32_t *src_base, uint32_t *
 // Walk and sum in one kernel with the sequence in shared memory (no scratch),
 // when every job's sequence fits; the two kernels above otherwise.
 bool jump_fused_fits(uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef);
+// njobs jobs on `grid` blocks (0: one block per job); with njobs_dev set (a
+// captured launch) the job count is read from *njobs_dev, at most njobs.
+// prepare_jump_fused raises the kernel's shared-memory limit for these sizes
+// (call it before capturing the launch).
 cudaError_t launch_jump_fused(const DevGen *gens, const uint32_t *src_base, uint32_t *dst_base, const DevJump *jobs,
-                              uint32_t njobs, uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef, cudaStream_t s);
+                              uint32_t njobs, uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef, cudaStream_t s,
+                              const uint32_t *njobs_dev = nullptr, uint32_t grid = 0);
+cudaError_t prepare_jump_fused(uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef);
 cudaError_t launch_jump_sum(const DevGen *gens, const uint32_t *seq_base, uint32_t *dst_base, const DevJump *jobs,
                             uint32_t njobs, uint32_t max_N, cudaStream_t s);
 
@@ -134,6 +140,10 @@ int report_error(int status, const char *msg);
 // whose status is ignored can leave an error there; the launch wrappers clear
 // it first, so that the check after a launch reports that launch alone.
 inline void clear_stale_error() { (void)cudaGetLastError(); }
+
+// Raises a kernel's dynamic shared-memory limit to at least dyn_bytes (never
+// lowers it: captured launches rely on the limit at replay).
+cudaError_t raise_smem_limit(const void *kernel, size_t dyn_bytes);
 
 bool threads_supported(uint32_t threads, uint32_t form);
 // Smallest compiled QMAX >= nq for this block size and form, 0 if none.

@@ -210,15 +210,13 @@ __device__ __forceinline__ uint32_t coef_bits(const uint32_t *cf, uint32_t i)
     return v & ((1u << R) - 1u);
 }
 
+// One job: walk, sum and step (Sec. 7) for jb, in the block's shared words.
 template <int R, int T>
-__global__ void __launch_bounds__(T, 2) k_jump_fused(const DevGen *gens, const uint32_t *src_base,
-                                                    uint32_t *dst_base, const DevJump *jobs, uint32_t seq_cap,
-                                                    uint32_t max_N)
+__device__ __forceinline__ void fused_job(const DevJump jb, const DevGen *gens, const uint32_t *src_base,
+                                          uint32_t *dst_base, uint32_t *sm, uint32_t *tbl, uint32_t seq_cap,
+                                          uint32_t max_N)
 {
-    extern __shared__ __align__(16) uint32_t sm[];
-    __shared__ uint32_t tbl[16];
     uint32_t *x = sm, *y = sm + seq_cap, *cf = sm + seq_cap + max_N;
-    const DevJump jb = jobs[blockIdx.x];
     const DevGen &g = gens[jb.gen];
     const uint32_t N = g.N, M = g.M, S = N - M, mask = g.mask, sh1 = g.sh1, sh2 = g.sh2;
     const uint32_t tid = threadIdx.x, ncoef = jb.ncoef;
@@ -280,6 +278,23 @@ __global__ void __launch_bounds__(T, 2) k_jump_fused(const DevGen *gens, const u
     if (tid == 0u) dst[N - 1u] = rec_word(y[0], y[1], y[M], mask, sh1, sh2, tbl);
 }
 
+// One job per block and round of the grid: jobs blockIdx.x, blockIdx.x +
+// gridDim.x, ... below njobs, or below *njobs_dev when that is set (a
+// captured launch, whose grid is fixed while its job count is not).
+template <int R, int T>
+__global__ void __launch_bounds__(T, 2) k_jump_fused(const DevGen *gens, const uint32_t *src_base,
+                                                    uint32_t *dst_base, const DevJump *jobs, uint32_t seq_cap,
+                                                    uint32_t max_N, uint32_t njobs, const uint32_t *njobs_dev)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ uint32_t tbl[16];
+    const uint32_t n = njobs_dev ? *njobs_dev : njobs;
+    for (uint32_t job = blockIdx.x; job < n; job += gridDim.x) {
+        fused_job<R, T>(jobs[job], gens, src_base, dst_base, sm, tbl, seq_cap, max_N);
+        __syncthreads();                                    // shared words reused by the next job
+    }
+}
+
 constexpr uint32_t kFusedThreads = 512;
 constexpr uint32_t kFusedR = 12;
 constexpr size_t kFusedSmemMax = 200u * 1024u;
@@ -298,10 +313,19 @@ bool jump_fused_fits(uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef)
     return max_N <= kFusedR * kFusedThreads && fused_smem((max_nseq + 3u) & ~3u, max_N, max_ncoef) <= kFusedSmemMax;
 }
 
+cudaError_t prepare_jump_fused(uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef)
+{
+    if (max_N < 3u || !jump_fused_fits(max_N, max_nseq, max_ncoef)) return cudaErrorInvalidValue;
+    const uint32_t seq_cap = (max_nseq + 3u) & ~3u;
+    return raise_smem_limit((const void *)k_jump_fused<kFusedR, kFusedThreads>, fused_smem(seq_cap, max_N, max_ncoef));
+}
+
 cudaError_t launch_jump_fused(const DevGen *gens, const uint32_t *src_base, uint32_t *dst_base, const DevJump *jobs,
-                              uint32_t njobs, uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef, cudaStream_t s)
+                              uint32_t njobs, uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef, cudaStream_t s,
+                              const uint32_t *njobs_dev, uint32_t grid)
 {
     if (!njobs) return cudaSuccess;
+    if (!grid || grid > njobs) grid = njobs;
     if (max_N < 3u || !jump_fused_fits(max_N, max_nseq, max_ncoef)) return cudaErrorInvalidValue;
     const uint32_t seq_cap = (max_nseq + 3u) & ~3u;
     const size_t smem = fused_smem(seq_cap, max_N, max_ncoef);
@@ -309,12 +333,12 @@ cudaError_t launch_jump_fused(const DevGen *gens, const uint32_t *src_base, uint
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return e;
-    if (smem + 64u > 48u * 1024u && cap == cudaStreamCaptureStatusNone) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cap == cudaStreamCaptureStatusNone) {
+        e = raise_smem_limit((const void *)k, smem);
         if (e != cudaSuccess) return e;
     }
     clear_stale_error();
-    k<<<njobs, kFusedThreads, smem, s>>>(gens, src_base, dst_base, jobs, seq_cap, max_N);
+    k<<<grid, kFusedThreads, smem, s>>>(gens, src_base, dst_base, jobs, seq_cap, max_N, njobs, njobs_dev);
     return cudaGetLastError();
 }
 

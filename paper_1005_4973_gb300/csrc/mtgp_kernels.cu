@@ -3,6 +3,9 @@
 // the write-only bandwidth probe, and the launchers.
 #include "mtgp_internal.h"
 
+#include <mutex>
+#include <unordered_map>
+
 namespace mtgp {
 
 namespace {
@@ -88,6 +91,22 @@ GenKernel pick(uint32_t threads, uint32_t form, uint32_t qmax, bool interleave =
 
 }  // namespace
 
+// A kernel's dynamic shared-memory limit is a function attribute that captured
+// graphs rely on at replay: it is only ever raised, never lowered below what an
+// earlier launch or capture used.
+cudaError_t raise_smem_limit(const void *kernel, size_t dyn_bytes)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void *, size_t> set;
+    if (dyn_bytes + 1024u <= 48u * 1024u) return cudaSuccess;   // within the default (static words aside)
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = set[kernel];
+    if (dyn_bytes <= cur) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_bytes);
+    if (e == cudaSuccess) cur = dyn_bytes;
+    return e;
+}
+
 // Slot counts compiled: MTGP_QMAX_LIST for forms 0-2, 1..4 groups for form 3.
 static const uint32_t kSlots[] = {MTGP_QMAX_LIST};
 static const uint32_t kWideSlots[] = {1, 2, 3, 4};
@@ -134,10 +153,10 @@ cudaError_t launch_generate(const LaunchArgs &a, uint32_t threads, uint32_t form
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return e;
-    // dynamic + the kernels' static words past the default limit (set before
-    // a capture by generate_occupancy; a function attribute is not captured)
-    if (smem + 1024u > 48u * 1024u && cap == cudaStreamCaptureStatusNone) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // dynamic words past the default limit (raised before a capture by
+    // generate_occupancy; a function attribute is not captured)
+    if (cap == cudaStreamCaptureStatusNone) {
+        e = raise_smem_limit((const void *)k, smem);
         if (e != cudaSuccess) return e;
     }
     clear_stale_error();
@@ -151,10 +170,8 @@ cudaError_t generate_occupancy(uint32_t threads, uint32_t form, uint32_t qmax, u
     GenKernel k = pick(threads, form, qmax, interleave);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = (size_t)buf_words * sizeof(uint32_t);
-    if (smem + 1024u > 48u * 1024u) {     // dynamic + the kernels' static words past the default
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = raise_smem_limit((const void *)k, smem);
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
 }
 

@@ -3,6 +3,7 @@
 // graph calls: each tick is one replay of the pool's captured persistent
 // launch, advancing every active request by up to `chunk` numbers.
 #include "mtgp.h"
+#include "mtgp_graph.h"
 #include "mtgp_internal.h"
 
 #include <algorithm>
@@ -150,7 +151,9 @@ mtgp_status mtgp_server_create(mtgp_pool *pool, const mtgp_server_config *cfg, v
                                                   : fail_cuda(e, "server: cudaMalloc arena");
         }
         s->free_list[0] = s->cfg.arena_bytes;
-        st = mtgp_graph_create(pool, std::min<uint32_t>(s->cfg.max_active, s->count), stream, &s->graph);
+        // ticks never split a request into jump-ahead pieces: that would need the
+        // annihilating polynomial of every generator a request may name
+        st = mtgp::graph_create(pool, std::min<uint32_t>(s->cfg.max_active, s->count), stream, false, &s->graph);
         if (st != MTGP_OK) {
             mtgp_server_destroy(s);
             return st;

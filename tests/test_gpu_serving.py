@@ -69,6 +69,52 @@ def test_graph_replays_with_changing_work(form):
     graph.close()
 
 
+@pytest.mark.parametrize("max_items", [256, None])
+def test_graph_replays_with_jump_ahead_pieces(max_items):
+    """The captured launch holds a jump kernel (Sec. 7) before the generation
+    kernel: long requests run as pieces whose start states each replay
+    computes from the generators' current states.  With room for only the
+    unsplit items (max_items = None: as many as the largest list), the plan
+    falls back to whole items.  Either way every replay matches the oracle
+    streams, in order."""
+    import paper_1005_4973_gb300 as M
+    pool = lib_pool(GENS)
+    pool.set_config(pieces=4, piece_log2=10)
+    rng = np.random.default_rng(7)
+    lists = []
+    for rep in range(3):
+        gens = sorted(rng.choice(len(GENS), size=int(rng.integers(3, len(GENS) + 1)), replace=False).tolist())
+        reqs, off = [], int(rng.integers(0, 4))
+        for g in gens:
+            n = int(rng.integers(1000, 120000))
+            reqs.append((g, int(rng.integers(0, 3)), n, off))
+            off += n + int(rng.integers(0, 4))
+        lists.append((reqs, off))
+    graph = M.Graph(pool, max_items=max_items or max(len(r) for r, _ in lists))
+    launches = []
+    for rep, (reqs, total) in enumerate(lists):
+        out = torch.zeros(total, dtype=torch.int32, device="cuda")
+        graph.set_requests(reqs, out)
+        for _ in range(1 + rep % 2):
+            before = pool.launch_count()
+            graph.launch()
+            torch.cuda.synchronize()
+            assert pool.launch_count() - before == 2          # jump, generation
+            launches.append((reqs, as_u32(out).copy()))
+    assert graph.errors() == 0
+    per_gen = {}
+    for reqs, _ in launches:
+        for g, dt, n, _ in reqs:
+            per_gen.setdefault(g, []).append((dt, n))
+    ref = _oracle_streams(GENS, per_gen)
+    cursor = {g: 0 for g in per_gen}
+    for reqs, o in launches:
+        for g, dt, n, off in reqs:
+            assert np.array_equal(o[off:off + n], ref[g][cursor[g]]), (g, dt, n)
+            cursor[g] += 1
+    graph.close()
+
+
 class _DevView:
     """Zero-copy int32 view of n words of device memory (CUDA array interface)."""
 

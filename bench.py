@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MTGP Gnum/s & HBM write GB/s vs peak (plain vs batched); served p50/p99 latency"
-KERNEL_SOURCES = ["paper_1005_4973_gb300/csrc/mtgp_device.cuh", "paper_1005_4973_gb300/csrc/mtgp_internal.h"]
+KERNEL_SOURCES = ["paper_1005_4973_gb300/csrc/mtgp_device.cuh", "paper_1005_4973_gb300/csrc/mtgp_layout.h"]
 NCU_SUMMARY = os.path.join(ROOT, "profiles", "k_generate_c2.md")
 
 

@@ -404,13 +404,20 @@ typedef struct mtgp_graph mtgp_graph;
 
 /* Captures the launch for pool p with the pool's configuration (persistent),
  * sized for every generator of the pool and at most max_items work items
- * (distinct generators) and max_items segments per replay.  Synchronous.
- * Errors: MTGP_EINVAL, MTGP_ENOMEM, MTGP_ECUDA. */
+ * and max_items segments per replay.  Unless the pool's configuration has
+ * pieces = 1, the capture also holds a jump launch (Sec. 7) before the
+ * generation launch, and the graph owns device room for max_items piece
+ * states (max_items x N words): long requests then run as jump-ahead pieces,
+ * each replay computing their start states from the generators' current
+ * states.  Synchronous.  Errors: MTGP_EINVAL, MTGP_ENOMEM, MTGP_ECUDA. */
 mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mtgp_graph **out);
 
 /* Sets the requests of the next replays: same contract as mtgp_pool_generate
  * (grouping, order, layouts, dev_out), stream-ordered on `stream`.  The work
- * list stays in place for later replays until the next call. */
+ * list stays in place for later replays until the next call.  Pieces are
+ * planned as for mtgp_pool_generate when they fit the graph's max_items and
+ * piece-state room, else the requests run as whole work items.  On an error
+ * the graph's work list is emptied (replays then generate nothing). */
 mtgp_status mtgp_graph_set_requests(mtgp_graph *g, const mtgp_request *reqs, uint32_t nreq, void *dev_out,
                                     mtgp_layout layout, void *stream);
 

@@ -1354,19 +1354,24 @@ mtgp_status mtgp_graph_set_requests(mtgp_graph *g, const mtgp_request *reqs, uin
         cudaStream_t s = (cudaStream_t)stream;
         mtgp_status st = pool_busy_check(p, s);
         if (st != MTGP_OK) return st;
-        if (((uintptr_t)dev_out & 3u) != 0) return fail(MTGP_EINVAL, "dev_out must be 4-byte aligned");
+        // on an error the work list in place is emptied: it may refer to jump
+        // polynomials that planning evicted from the cache
+        auto invalidate = [&](mtgp_status r) {
+            (void)cudaMemsetAsync((char *)g->d_buf + 8u, 0, sizeof(uint32_t), s);
+            (void)cudaMemsetAsync((char *)g->d_buf + 24u, 0, sizeof(uint32_t), s);
+            return r;
+        };
+        if (((uintptr_t)dev_out & 3u) != 0) return invalidate(fail(MTGP_EINVAL, "dev_out must be 4-byte aligned"));
         if (g->form == 3u && layout != MTGP_LAYOUT_BLOCKED)
-            return fail(MTGP_EINVAL, "graph: the wide form (3) it captured writes blocked layouts only");
+            return invalidate(fail(MTGP_EINVAL, "graph: the wide form (3) it captured writes blocked layouts only"));
         const mtgp_config saved = p->cfg;
         p->cfg.persistent = 1u;                              // longest-first order for the fixed grid
         Plan plan;
         st = build_plan(p, reqs, nreq, layout, &plan);
-        bool split = false;
         if (st == MTGP_OK && g->jump) {
             // pieces (Sec. 7) as in a pool call, when they fit the captured
             // capacity and the captured jump kernel; otherwise whole items
             Plan pieces = plan;
-            split = true;
             st = split_plan(p, &pieces, s);
             const bool fits = pieces.work.size() <= g->max_items && pieces.segs.size() <= g->max_items &&
                               pieces.jobs.size() <= g->max_items && pieces.jstate_words <= g->jstate_cap &&
@@ -1375,15 +1380,6 @@ mtgp_status mtgp_graph_set_requests(mtgp_graph *g, const mtgp_request *reqs, uin
             if (st == MTGP_OK && fits) plan = std::move(pieces);
         }
         p->cfg = saved;
-        // the work list in place refers to jump polynomials that planning may
-        // have evicted from the cache: replays do nothing until a new list is in
-        auto invalidate = [&](mtgp_status r) {
-            if (split) {
-                (void)cudaMemsetAsync((char *)g->d_buf + 8u, 0, sizeof(uint32_t), s);
-                (void)cudaMemsetAsync((char *)g->d_buf + 24u, 0, sizeof(uint32_t), s);
-            }
-            return r;
-        };
         if (st != MTGP_OK) return invalidate(st);
         if (plan.work.size() > g->max_items || plan.segs.size() > g->max_items)
             return invalidate(fail(MTGP_EINVAL, "graph: %zu work items / %zu segments exceed its capacity %u",

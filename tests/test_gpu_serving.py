@@ -115,6 +115,29 @@ def test_graph_replays_with_jump_ahead_pieces(max_items):
     graph.close()
 
 
+def test_graph_set_requests_error_empties_the_list():
+    """After a failed set_requests the graph's list is empty: a replay then
+    writes nothing and advances no stream."""
+    import paper_1005_4973_gb300 as M
+    pool = lib_pool(GENS[:4])
+    pool.set_config(pieces=4, piece_log2=10)
+    graph = M.Graph(pool, max_items=64)
+    out = torch.zeros(50000, dtype=torch.int32, device="cuda")
+    graph.set_requests([(0, 0, 30000, 0), (1, 1, 20000, 30000)], out)
+    graph.launch()
+    torch.cuda.synchronize()
+    pos = [pool.position(i) for i in range(4)]
+    assert pos[:2] == [30000, 20000]
+    with pytest.raises(M.MTGPError):
+        graph.set_requests([(0, 0, 10, 0), (9, 0, 10, 10)], out)     # generator 9 is not in the pool
+    out.fill_(7)
+    graph.launch()
+    torch.cuda.synchronize()
+    assert [pool.position(i) for i in range(4)] == pos
+    assert bool((out == 7).all())
+    graph.close()
+
+
 class _DevView:
     """Zero-copy int32 view of n words of device memory (CUDA array interface)."""
 

@@ -409,7 +409,11 @@ typedef struct mtgp_graph mtgp_graph;
  * generation launch, and the graph owns device room for max_items piece
  * states (max_items x N words): long requests then run as jump-ahead pieces,
  * each replay computing their start states from the generators' current
- * states.  Synchronous.  Errors: MTGP_EINVAL, MTGP_ENOMEM, MTGP_ECUDA. */
+ * states.  mtgp_pool_load, and any call on the pool that has to evict cached
+ * jump polynomials (more than 1 GiB of them), empty the work lists of the
+ * pool's graphs that hold pieces: their replays generate nothing until the
+ * next mtgp_graph_set_requests.  Destroy a pool's graphs before the pool.
+ * Synchronous.  Errors: MTGP_EINVAL, MTGP_ENOMEM, MTGP_ECUDA. */
 mtgp_status mtgp_graph_create(mtgp_pool *p, uint32_t max_items, void *stream, mtgp_graph **out);
 
 /* Sets the requests of the next replays: same contract as mtgp_pool_generate

@@ -179,6 +179,9 @@ struct mtgp_pool {
     uint64_t jstate_words = 0;
     uint32_t *d_seq = nullptr;
     uint64_t seq_words = 0;
+    // graphs whose work lists may hold jump jobs, which point at polynomials
+    // in jc: emptied before those polynomials are freed
+    std::vector<mtgp_graph *> jump_graphs;
 };
 
 struct mtgp_state {
@@ -187,7 +190,8 @@ struct mtgp_state {
 
 // A captured persistent launch (see mtgp_graph_create).  Device buffer layout:
 // [0] work counter, [4] error word, [8] work-item count, [16] output base
-// pointer, [256 ..) DevWork[max_items], then DevSeg[max_items].
+// pointer, [24] jump-job count, [256 ..) DevWork[max_items], then
+// DevSeg[max_items], then (with pieces) DevJump[max_items].
 struct mtgp_graph {
     mtgp_pool *pool = nullptr;
     uint32_t max_items = 0;
@@ -210,6 +214,23 @@ struct mtgp_graph {
     uint64_t jstate_cap = 0;                 // words
     uint32_t j_max_N = 0, j_max_nseq = 0, j_max_ncoef = 0;
 };
+
+namespace {
+
+// Empties the work lists of the pool's graphs that may hold jump jobs (their
+// replays then generate nothing until the next set_requests): called, after
+// the pool's work finished, before cached jump polynomials are freed.
+mtgp_status empty_graph_lists(mtgp_pool *p)
+{
+    for (mtgp_graph *g : p->jump_graphs) {
+        CU(cudaMemsetAsync((char *)g->d_buf + 8u, 0, sizeof(uint32_t), nullptr), "empty graph work list");
+        CU(cudaMemsetAsync((char *)g->d_buf + 24u, 0, sizeof(uint32_t), nullptr), "empty graph jump list");
+    }
+    if (!p->jump_graphs.empty()) CU(cudaStreamSynchronize(nullptr), "cudaStreamSynchronize");
+    return MTGP_OK;
+}
+
+}  // namespace
 
 namespace {
 
@@ -562,6 +583,7 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
     if (st != MTGP_OK) return (mtgp_status)st;
     if (p->jc.dev_bytes > kJumpStoreCap) {
         mtgp_status r = pool_sync(p);
+        if (r == MTGP_OK) r = empty_graph_lists(p);
         if (r != MTGP_OK) return r;
         jump_clear(p->jc, false);
     }
@@ -1077,6 +1099,8 @@ mtgp_status mtgp_pool_load(mtgp_pool *p, const void *host_buf, size_t bytes)
         CU(cudaMemcpy(p->d_state, (const char *)host_buf + 16 + sizeof(DevGen) * p->count, 4u * p->state_words,
                       cudaMemcpyHostToDevice),
            "load states");
+        st = empty_graph_lists(p);   // their jump jobs were planned for the replaced states
+        if (st != MTGP_OK) return st;
         jump_clear(p->jc, true);   // annihilators belong to the replaced states
         return MTGP_OK;
     });
@@ -1333,6 +1357,7 @@ mtgp_status mtgp::graph_create(mtgp_pool *p, uint32_t max_items, void *stream, b
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamEndCapture"));
         CUG(cudaGraphInstantiate(&g->exec, g->graph, 0), "cudaGraphInstantiate");
     #undef CUG
+        if (g->jump) p->jump_graphs.push_back(g);
         *out = g;
         return MTGP_OK;
     });
@@ -1447,6 +1472,10 @@ mtgp_status mtgp_graph_errors(mtgp_graph *g, uint32_t *flags)
 void mtgp_graph_destroy(mtgp_graph *g)
 {
     if (!g) return;
+    if (g->pool) {
+        auto &v = g->pool->jump_graphs;
+        v.erase(std::remove(v.begin(), v.end(), g), v.end());
+    }
     if (g->pool && g->pool->used) cudaEventSynchronize(g->pool->ev_done);
     for (int k = 0; k < 2; ++k) {
         if (g->stage_used[k]) cudaEventSynchronize(g->ev_stage[k]);
@@ -1492,6 +1521,7 @@ mtgp_status mtgp_pool_jump(mtgp_pool *p, uint32_t i, uint64_t steps, void *strea
         if (r != MTGP_OK) return (mtgp_status)r;
         if (p->jc.dev_bytes > kJumpStoreCap) {
             st = pool_sync(p);
+            if (st == MTGP_OK) st = empty_graph_lists(p);
             if (st != MTGP_OK) return st;
             jump_clear(p->jc, false);
         }

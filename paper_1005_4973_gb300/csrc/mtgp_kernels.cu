@@ -3,8 +3,9 @@
 // the write-only bandwidth probe, and the launchers.
 #include "mtgp_internal.h"
 
+#include <map>
 #include <mutex>
-#include <unordered_map>
+#include <utility>
 
 namespace mtgp {
 
@@ -97,10 +98,13 @@ GenKernel pick(uint32_t threads, uint32_t form, uint32_t qmax, bool interleave =
 cudaError_t raise_smem_limit(const void *kernel, size_t dyn_bytes)
 {
     static std::mutex mu;
-    static std::unordered_map<const void *, size_t> set;
+    static std::map<std::pair<int, const void *>, size_t> set;  // (device, kernel) -> limit set
     if (dyn_bytes + 1024u <= 48u * 1024u) return cudaSuccess;   // within the default (static words aside)
+    int dev = 0;
+    const cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return de;
     std::lock_guard<std::mutex> lock(mu);
-    size_t &cur = set[kernel];
+    size_t &cur = set[{dev, kernel}];
     if (dyn_bytes <= cur) return cudaSuccess;
     const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_bytes);
     if (e == cudaSuccess) cur = dyn_bytes;

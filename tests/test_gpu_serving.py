@@ -138,6 +138,34 @@ def test_graph_set_requests_error_empties_the_list():
     graph.close()
 
 
+def test_pool_load_empties_graph_lists_with_pieces():
+    """mtgp_pool_load replaces the states the graph's jump jobs were planned
+    for: the graph's list is emptied (a replay writes nothing), and a new
+    set_requests continues from the loaded states exactly."""
+    import paper_1005_4973_gb300 as M
+    gens = GENS[:3]
+    pool = lib_pool(gens)
+    pool.set_config(pieces=4, piece_log2=10)
+    saved = pool.save()
+    graph = M.Graph(pool, max_items=64)
+    reqs = [(0, 0, 40000, 0), (1, 2, 30000, 40000), (2, 1, 20000, 70000)]
+    out = torch.zeros(90000, dtype=torch.int32, device="cuda")
+    graph.set_requests(reqs, out)
+    graph.launch()
+    torch.cuda.synchronize()
+    first = as_u32(out).copy()
+    pool.load(saved)                                     # back to the seeded states
+    out.fill_(7)
+    graph.launch()
+    torch.cuda.synchronize()
+    assert bool((out == 7).all()) and [pool.position(i) for i in range(3)] == [0, 0, 0]
+    graph.set_requests(reqs, out)
+    graph.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(as_u32(out), first)            # the same numbers again from the same states
+    graph.close()
+
+
 class _DevView:
     """Zero-copy int32 view of n words of device memory (CUDA array interface)."""
 

@@ -324,8 +324,10 @@ void mtgp_pool_destroy(mtgp_pool *p);
  * for this pool by timing candidate configurations on `stream` with the given
  * requests written to dev_scratch (caller-owned, large enough for them).  The
  * generators' states are saved before and restored after, so tuning does not
- * advance any stream.  On success the best configuration is set on the pool
- * and copied to *best (if not NULL); *best_ms receives its time (if not NULL).
+ * advance any stream (the restore empties the work lists of the pool's graphs
+ * that hold jump-ahead pieces, as mtgp_pool_load does).  On success the best
+ * configuration is set on the pool and copied to *best (if not NULL);
+ * *best_ms receives its time (if not NULL).
  * Synchronous.
  */
 mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_scratch,

@@ -1109,6 +1109,7 @@ mtgp_status mtgp_pool_load(mtgp_pool *p, const void *host_buf, size_t bytes)
 void mtgp_pool_destroy(mtgp_pool *p)
 {
     if (!p) return;
+    for (mtgp_graph *g : p->jump_graphs) g->pool = nullptr;   // graphs destroyed late must not reach back
     if (p->used && p->ev_done) cudaEventSynchronize(p->ev_done);
     if (p->copy_stream) cudaStreamSynchronize(p->copy_stream);
     if (p->upload_pending && p->ev_upload) cudaEventSynchronize(p->ev_upload);

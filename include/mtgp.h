@@ -127,7 +127,8 @@ typedef struct mtgp_config {
                                   on separate blocks, piece m starting from the state
                                   m L numbers ahead, computed on the GPU before the
                                   launch; outputs are identical.  0 = auto (about 16
-                                  blocks per SM), 1 = never split                    */
+                                  blocks per SM; up to 64 per generator), 1 = never
+                                  split, else at most 256                           */
     uint32_t piece_log2;       /* pieces hold at least 2^piece_log2 numbers; 0 = 20,
                                   else 10 .. 40                                    */
 } mtgp_config;

@@ -248,7 +248,7 @@ mtgp_status check_config(const mtgp_config &c)
     if (c.chunk < 32u || (c.chunk & (c.chunk - 1u)))
         return fail(MTGP_EINVAL, "chunk must be a power of two >= 32, got %u", c.chunk);
     if (c.buffer_words > 57344u) return fail(MTGP_EINVAL, "buffer_words must be <= 57344 (224 KiB)");
-    if (c.pieces > 64u) return fail(MTGP_EINVAL, "pieces must be <= 64");
+    if (c.pieces > 256u) return fail(MTGP_EINVAL, "pieces must be <= 256");
     if (c.piece_log2 != 0u && (c.piece_log2 < 10u || c.piece_log2 > 40u))
         return fail(MTGP_EINVAL, "piece_log2 must be 0 or in [10, 40]");
     return MTGP_OK;

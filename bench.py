@@ -59,6 +59,7 @@ WORKLOAD_DESC = {
     "c4": "C4: 8192 generators, mixed mexp, log-uniform 2^10..2^24, persistent",
     "c2s": "C2 at 2^20 numbers per generator (profiling size)",
     "c2m": "C2 at 2^22 numbers per generator (profiling size, split into pieces)",
+    "c3s": "C3 at 2^22 numbers per generator (profiling size, split into pieces)",
     "paper": "Sec. 4.4: 5e7 f[0,1) numbers from 108 MTGP11213 generators",
 }
 
@@ -68,6 +69,7 @@ def workload(name: str, rank: int):
     wl = {"c1": WL.c1, "c2": WL.c2, "c3": WL.c3, "c4": WL.c4,
           "c2s": lambda: WL.c2(n=1 << 20),
           "c2m": lambda: WL.c2(n=1 << 22),
+          "c3s": lambda: WL.c3(n=1 << 22),
           "paper": lambda: WL.paper()}[name]()
     if rank:
         for g in wl.gens:                  # distinct streams per rank
@@ -350,7 +352,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c2s", "c2m", "paper"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c2s", "c2m", "c3s", "paper"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -381,7 +383,7 @@ def main():
     wl = workload(args.workload, rank)
     ps = [M.mtgp_params_draw(g.mexp, g.param_seed, g.id) for g in wl.gens]
     pool = M.Pool(ps, [g.gen_id for g in wl.gens], [g.seed for g in wl.gens])
-    if args.workload in ("c3", "c4"):
+    if args.workload in ("c3", "c3s", "c4"):
         pool.set_config(persistent=1)
     if args.config:
         pool.set_config(**json.loads(args.config))

@@ -282,7 +282,7 @@ __device__ __forceinline__ void fused_job(const DevJump jb, const DevGen *gens, 
 // gridDim.x, ... below njobs, or below *njobs_dev when that is set (a
 // captured launch, whose grid is fixed while its job count is not).
 template <int R, int T>
-__global__ void __launch_bounds__(T, 2) k_jump_fused(const DevGen *gens, const uint32_t *src_base,
+__global__ void __launch_bounds__(T, T >= 1024 ? 1 : 2) k_jump_fused(const DevGen *gens, const uint32_t *src_base,
                                                     uint32_t *dst_base, const DevJump *jobs, uint32_t seq_cap,
                                                     uint32_t max_N, uint32_t njobs, const uint32_t *njobs_dev)
 {
@@ -296,8 +296,10 @@ __global__ void __launch_bounds__(T, 2) k_jump_fused(const DevGen *gens, const u
 }
 
 constexpr uint32_t kFusedThreads = 512;
+constexpr uint32_t kFusedThreadsBig = 1024;   // when one block fills an SM's shared memory
 constexpr uint32_t kFusedR = 12;
 constexpr size_t kFusedSmemMax = 200u * 1024u;
+constexpr size_t kFusedTwoBlocks = 113u * 1024u;  // two blocks of this much fit on an SM
 
 // Sequence window: the sum reads up to word ncoef - 1 + R + (N rounded up to
 // a lane's R words) + R - 1 < ncoef + N + 3R.
@@ -313,11 +315,25 @@ bool jump_fused_fits(uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef)
     return max_N <= kFusedR * kFusedThreads && fused_smem((max_nseq + 3u) & ~3u, max_N, max_ncoef) <= kFusedSmemMax;
 }
 
+namespace {
+
+// The fused kernel for a launch whose blocks need smem bytes: 512 threads
+// when two blocks fit on an SM, else 1024 (one block, twice the warps to hide
+// the sum's latency; measured on MTGP44497-sized jobs).
+void (*fused_kernel(size_t smem))(const DevGen *, const uint32_t *, uint32_t *, const DevJump *, uint32_t, uint32_t,
+                                  uint32_t, const uint32_t *)
+{
+    return smem > kFusedTwoBlocks ? k_jump_fused<kFusedR, kFusedThreadsBig> : k_jump_fused<kFusedR, kFusedThreads>;
+}
+
+}  // namespace
+
 cudaError_t prepare_jump_fused(uint32_t max_N, uint32_t max_nseq, uint32_t max_ncoef)
 {
     if (max_N < 3u || !jump_fused_fits(max_N, max_nseq, max_ncoef)) return cudaErrorInvalidValue;
     const uint32_t seq_cap = (max_nseq + 3u) & ~3u;
-    return raise_smem_limit((const void *)k_jump_fused<kFusedR, kFusedThreads>, fused_smem(seq_cap, max_N, max_ncoef));
+    const size_t smem = fused_smem(seq_cap, max_N, max_ncoef);
+    return raise_smem_limit((const void *)fused_kernel(smem), smem);
 }
 
 cudaError_t launch_jump_fused(const DevGen *gens, const uint32_t *src_base, uint32_t *dst_base, const DevJump *jobs,
@@ -329,7 +345,8 @@ cudaError_t launch_jump_fused(const DevGen *gens, const uint32_t *src_base, uint
     if (max_N < 3u || !jump_fused_fits(max_N, max_nseq, max_ncoef)) return cudaErrorInvalidValue;
     const uint32_t seq_cap = (max_nseq + 3u) & ~3u;
     const size_t smem = fused_smem(seq_cap, max_N, max_ncoef);
-    auto k = k_jump_fused<kFusedR, kFusedThreads>;
+    auto k = fused_kernel(smem);
+    const uint32_t threads = smem > kFusedTwoBlocks ? kFusedThreadsBig : kFusedThreads;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return e;
@@ -338,7 +355,7 @@ cudaError_t launch_jump_fused(const DevGen *gens, const uint32_t *src_base, uint
         if (e != cudaSuccess) return e;
     }
     clear_stale_error();
-    k<<<grid, kFusedThreads, smem, s>>>(gens, src_base, dst_base, jobs, seq_cap, max_N, njobs, njobs_dev);
+    k<<<grid, threads, smem, s>>>(gens, src_base, dst_base, jobs, seq_cap, max_N, njobs, njobs_dev);
     return cudaGetLastError();
 }
 

@@ -219,7 +219,7 @@ def run_batched(torch, M, sample: int = 512):
     # about 16 work items' worth per SM)
     graph = M.Graph(pool, max_items=2 * len(wl.gens))
     graph.set_requests(wl.requests, out)
-    for _ in range(2):
+    for _ in range(3):                                       # warm-up replays
         graph.launch()
     steps = 3
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

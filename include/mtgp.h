@@ -535,13 +535,18 @@ void mtgp_server_destroy(mtgp_server *s);
  * until the process exits.  count > MTGP_NOALLOC_MAX_GENS or
  * nreq > MTGP_NOALLOC_MAX_REQS returns MTGP_EINVAL with a message.  The first
  * call on each device looks up that array's device address (a one-time
- * set-up).  The records are copied out of the call's own host memory, so a
- * stream being captured into a CUDA graph is refused (MTGP_EINVAL).  Every call
- * shares the array and overwrites it (its control words are cleared on each
- * call), so calls that overlap on the GPU -- on different streams, or from
- * several host threads -- race; order them on one stream.  The records are
- * copied from ordinary host memory, so the call waits for work already
- * queued on `stream` before it returns.
+ * set-up; make that first call before any stream capture).  The records are
+ * copied out of the call's own host memory, so a stream being captured into a
+ * CUDA graph is refused (MTGP_EINVAL).  Every call shares the array and
+ * overwrites it (its control words are cleared on each call).  The library
+ * holds a lock from a call's copy through its launch, so calls from several
+ * host threads on ONE stream queue one after the other and are safe; calls
+ * whose work overlaps on the GPU (different streams) race on the array and
+ * must not be made.  Overlapping state ranges (two generators sharing words)
+ * return MTGP_EINVAL.  The launch shape is sized on the host so that the
+ * kernel's buffer check always passes; kernel-side errors therefore cannot
+ * occur on this path.  The records are copied from ordinary host memory, so
+ * the call may wait for work already queued on `stream` before it returns.
  */
 #define MTGP_NOALLOC_SCRATCH_BYTES 32768u
 #define MTGP_NOALLOC_MAX_GENS 64u

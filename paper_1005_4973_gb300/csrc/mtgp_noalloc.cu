@@ -8,9 +8,13 @@
 #include "mtgp.h"
 #include "mtgp_internal.h"
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <mutex>
+#include <new>
+#include <utility>
 #include <vector>
 
 using namespace mtgp;
@@ -28,6 +32,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[MTGP_NOALLOC_SC
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
+// Held from the copy of a call's records into the array through the launch
+// of its kernel, so that calls from several host threads on one stream queue
+// as copy, kernel, copy, kernel: each kernel then reads its own records.
+std::mutex g_call_mu;
 void *g_scratch_addr[kMaxDevices] = {};   // device address of g_noalloc_scratch per device
 
 mtgp_status fail(mtgp_status st, const char *msg) { return (mtgp_status)report_error(st, msg); }
@@ -62,9 +70,11 @@ size_t align16(size_t x) { return (x + 15u) & ~(size_t)15u; }
 
 }  // namespace
 
-extern "C" mtgp_status mtgp_generate_noalloc(const mtgp_params *ps, uint32_t count, uint32_t *dev_states,
-                                             const uint64_t *state_offsets, const mtgp_request *reqs,
-                                             uint32_t nreq, void *dev_out, void *stream)
+namespace {
+
+mtgp_status generate_noalloc(const mtgp_params *ps, uint32_t count, uint32_t *dev_states,
+                             const uint64_t *state_offsets, const mtgp_request *reqs, uint32_t nreq,
+                             void *dev_out, void *stream)
 {
     if (!ps || !state_offsets || !dev_states || count == 0)
         return fail(MTGP_EINVAL, "noalloc: NULL parameters, states or offsets, or count == 0");
@@ -104,6 +114,16 @@ extern "C" mtgp_status mtgp_generate_noalloc(const mtgp_params *ps, uint32_t cou
         nmax = g.N > nmax ? g.N : nmax;
         smax = g.N - g.M > smax ? g.N - g.M : smax;
     }
+    // two generators whose state ranges overlap would run in two blocks that
+    // read and write the same words at once: refused
+    {
+        std::vector<std::pair<uint64_t, uint64_t>> rng(count);
+        for (uint32_t i = 0; i < count; ++i) rng[i] = {state_offsets[i], state_offsets[i] + gens[i].N};
+        std::sort(rng.begin(), rng.end());
+        for (uint32_t i = 1; i < count; ++i)
+            if (rng[i].first < rng[i - 1].second)
+                return fail(MTGP_EINVAL, "noalloc: the state ranges of two generators overlap");
+    }
     // requests grouped per generator, in array order (blocked layout)
     std::vector<DevWork> work;
     std::vector<DevSeg> segs;
@@ -142,6 +162,15 @@ extern "C" mtgp_status mtgp_generate_noalloc(const mtgp_params *ps, uint32_t cou
     const uint32_t need = 2u * nmax + span + 32u;
     if (B > 12288u) B = 12288u;                      // 48 KiB of shared memory per block
     if (B < need) B = need;
+    // The kernel raises its buffer error (and skips the item) only when a
+    // generator's slot count exceeds qmax or its buffer minimum exceeds B.
+    // Both hold here for every generator, so the kernel's error word, which
+    // no call reads back, cannot be set on this path.
+    for (uint32_t i = 0; i < count; ++i) {
+        const uint32_t S = gens[i].N - gens[i].M, nq = (S + threads - 1u) / threads;
+        if (nq > qmax || 2u * gens[i].N + nq * threads + 32u > B)
+            return fail(MTGP_EINVAL, "noalloc: internal launch shape does not fit a generator");
+    }
     // one image of the scratch: control words zeroed, then the records
     const size_t gb = align16(sizeof(DevGen) * count), wb = align16(sizeof(DevWork) * work.size());
     const size_t bytes = 256u + gb + wb + sizeof(DevSeg) * segs.size();
@@ -160,6 +189,7 @@ extern "C" mtgp_status mtgp_generate_noalloc(const mtgp_params *ps, uint32_t cou
     void *base = nullptr;
     mtgp_status st = scratch_address(&base);
     if (st != MTGP_OK) return st;
+    std::lock_guard<std::mutex> lock(g_call_mu);
     cudaError_t e = cudaMemcpyAsync(base, image.data(), bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail_cuda(e, "noalloc: copy records to scratch");
     unsigned char *b = (unsigned char *)base;
@@ -177,4 +207,21 @@ extern "C" mtgp_status mtgp_generate_noalloc(const mtgp_params *ps, uint32_t cou
     e = launch_generate(a, threads, 0u, qmax, (uint32_t)work.size(), s);
     if (e != cudaSuccess) return fail_cuda(e, "noalloc: generate kernel launch");
     return MTGP_OK;
+}
+
+}  // namespace
+
+// The records are built in host containers; a failed host allocation comes
+// back as MTGP_ENOMEM instead of an exception crossing the C ABI.
+extern "C" mtgp_status mtgp_generate_noalloc(const mtgp_params *ps, uint32_t count, uint32_t *dev_states,
+                                             const uint64_t *state_offsets, const mtgp_request *reqs,
+                                             uint32_t nreq, void *dev_out, void *stream)
+{
+    try {
+        return generate_noalloc(ps, count, dev_states, state_offsets, reqs, nreq, dev_out, stream);
+    } catch (const std::bad_alloc &) {
+        return fail(MTGP_ENOMEM, "noalloc: host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(MTGP_EINVAL, e.what());
+    }
 }

@@ -15,7 +15,6 @@ import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
-pytestmark = pytest.mark.gpu
 
 
 def _lib():
@@ -34,6 +33,7 @@ def _noalloc(L, ps, states, offsets, reqs, out, stream):
                                        out.data_ptr(), stream)
 
 
+@pytest.mark.gpu
 def test_noalloc_matches_pool_path_over_two_calls():
     M, L = _lib()
     assert torch.cuda.is_available()
@@ -68,6 +68,7 @@ def test_noalloc_matches_pool_path_over_two_calls():
     pool.close()
 
 
+@pytest.mark.gpu
 def test_noalloc_rejects_calls_beyond_its_scratch():
     M, L = _lib()
     p = M.mtgp_params_draw(11213, 1, 0)
@@ -83,6 +84,7 @@ def test_noalloc_rejects_calls_beyond_its_scratch():
     assert st == L.MTGP_EINVAL and "scratch limit" in L.last_error()
 
 
+@pytest.mark.gpu
 def test_noalloc_refuses_a_stream_under_capture():
     # the records are copied out of the call's own host memory, so a captured
     # copy would replay from memory that is gone: the call is refused before it
@@ -105,3 +107,23 @@ def test_noalloc_refuses_a_stream_under_capture():
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
     pool.close()
+
+
+def test_noalloc_refuses_overlapping_state_ranges():
+    # Two generators whose N-word states overlap would run in two blocks that
+    # read and write the same words at once.  The call refuses them on the
+    # host, before it touches the device, so this runs without a GPU (the
+    # buffer addresses below are never dereferenced).
+    from paper_1005_4973_gb300 import build
+    build.build()
+    from paper_1005_4973_gb300 import _lib as L
+    import paper_1005_4973_gb300 as M
+    p = M.mtgp_params_draw(11213, 1, 0)
+    q = M.mtgp_params_draw(11213, 2, 1)
+    fake_states, fake_out = 0x10000, 0x20000
+    parr = (L.mtgp_params * 2)(p, q)
+    rarr = L.requests_array([(0, 0, 16, 0), (1, 0, 16, 16)])
+    for offs in ([0, 100], [350, 0], [0, 0], [400, 50]):
+        o = (ctypes.c_uint64 * 2)(*offs)
+        st = L.LIB.mtgp_generate_noalloc(parr, 2, fake_states, o, rarr, 2, fake_out, None)
+        assert st == L.MTGP_EINVAL and "overlap" in L.last_error(), offs

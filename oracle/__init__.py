@@ -94,6 +94,8 @@ def lib():
             "orc_params_sizeof": (ctypes.c_int, []),
             "orc_kv": (ctypes.c_int, [u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_int)]),
             "orc_mt19937_outputs": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, u32p]),
+            "orc_mt19937_init_genrand": (None, [ctypes.c_uint32, u32p]),
+            "orc_mt19937_outputs_from": (ctypes.c_int, [u32p, ctypes.c_int, u32p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -268,6 +270,16 @@ def kv(seq: np.ndarray, p: int, vmax: int = 32) -> np.ndarray:
 def mt19937_outputs(seed: int, n: int) -> np.ndarray:
     out = np.zeros(n, dtype=np.uint32)
     if lib().orc_mt19937_outputs(seed, n, _p(out, ctypes.c_uint32)):
+        raise MemoryError("oracle allocation failed")
+    return out
+
+
+def mt19937_outputs_init_genrand(seed: int, n: int) -> np.ndarray:
+    """n outputs of MT19937 seeded by the published 32-bit seeding routine."""
+    st = np.zeros(624, dtype=np.uint32)
+    lib().orc_mt19937_init_genrand(seed, _p(st, ctypes.c_uint32))
+    out = np.zeros(n, dtype=np.uint32)
+    if lib().orc_mt19937_outputs_from(_p(st, ctypes.c_uint32), n, _p(out, ctypes.c_uint32)):
         raise MemoryError("oracle allocation failed")
     return out
 

@@ -21,8 +21,12 @@
  *                                      prints for MT19937 (Sec. 3.8), the bound
  *                                      k(v) <= floor(p / v) and k(1) = p at full
  *                                      period
- *   orc_mt19937_outputs                the published MT19937 (Matsumoto and
- *                                      Nishimura 1998), only as the k(v) pin's input
+ *   orc_mt19937_*                      the published MT19937 (Matsumoto and
+ *                                      Nishimura 1998), only as the k(v) pin's input;
+ *                                      pinned by ISO C++'s required 10000th output of
+ *                                      std::mt19937 and by numpy's MT19937
+ *   orc_splitmix64_next / orc_mix64    pinned by the published SplitMix64 outputs for
+ *                                      seed 0 (tests/golden/splitmix64_seed0.txt)
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -573,14 +577,24 @@ int orc_kv(const uint32_t *seq, int L, int p, int vmax, int *kv)
  * 0x9d2c5680 and 0xefc60000.  State filled by SplitMix64 from `seed` (any
  * nonzero state will do for orc_kv).  Straight array, n outputs.
  */
-int orc_mt19937_outputs(uint64_t seed, int n, uint32_t *out)
+/* The published MT19937 seeding by one 32-bit integer (Matsumoto and
+ * Nishimura's init_genrand): x_0 = s, x_j = 1812433253 (x_{j-1} xor
+ * (x_{j-1} >> 30)) + j mod 2^32.  With s = 5489 it is the state of a
+ * default-constructed std::mt19937 in ISO C++. */
+void orc_mt19937_init_genrand(uint32_t s, uint32_t *x624)
+{
+    x624[0] = s;
+    for (uint32_t j = 1; j < 624u; j++)
+        x624[j] = 1812433253u * (x624[j - 1] ^ (x624[j - 1] >> 30)) + j;
+}
+
+/* n outputs of MT19937 from the 624-word state x624 (oldest word first). */
+int orc_mt19937_outputs_from(const uint32_t *x624, int n, uint32_t *out)
 {
     const int N = 624, M = 397;
     uint32_t *x = (uint32_t *)malloc(((size_t)N + (size_t)n) * 4u);
     if (!x) return -1;
-    uint64_t s = seed;
-    for (int j = 0; j < N; j++) x[j] = (uint32_t)orc_splitmix64_next(&s);
-    x[0] |= 0x80000000u;                          /* the upper bit of x_0 is state: nonzero */
+    memcpy(x, x624, (size_t)N * 4u);
     for (int i = 0; i < n; i++) {
         const uint32_t y = (x[i] & 0x80000000u) | (x[i + 1] & 0x7fffffffu);
         x[N + i] = x[i + M] ^ (y >> 1) ^ ((y & 1u) ? 0x9908b0dfu : 0u);
@@ -593,6 +607,17 @@ int orc_mt19937_outputs(uint64_t seed, int n, uint32_t *out)
     }
     free(x);
     return 0;
+}
+
+/* n outputs of MT19937 from a state of SplitMix64 words keyed by `seed` (any
+ * nonzero state serves the k(v) pin, which does not depend on the state). */
+int orc_mt19937_outputs(uint64_t seed, int n, uint32_t *out)
+{
+    uint32_t x[624];
+    uint64_t s = seed;
+    for (int j = 0; j < 624; j++) x[j] = (uint32_t)orc_splitmix64_next(&s);
+    x[0] |= 0x80000000u;                          /* the upper bit of x_0 is state: nonzero */
+    return orc_mt19937_outputs_from(x, n, out);
 }
 
 /* Size of the parameter struct, so the Python side can check its mirror. */

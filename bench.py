@@ -31,8 +31,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MTGP Gnum/s & HBM write GB/s vs peak (plain vs batched); served p50/p99 latency"
-KERNEL_SOURCES = ["paper_1005_4973_gb300/csrc/mtgp_device.cuh", "paper_1005_4973_gb300/csrc/mtgp_layout.h"]
-NCU_SUMMARY = os.path.join(ROOT, "profiles", "k_generate_c2.md")
+KERNEL_SOURCES = ["paper_1005_4973_gb300/csrc/mtgp_device.cuh", "paper_1005_4973_gb300/csrc/mtgp_pairs.cuh",
+                  "paper_1005_4973_gb300/csrc/mtgp_layout.h"]
+# generation kernel of each launch form (mtgp_config.form)
+FORM_KERNEL = {0: "k_generate", 1: "k_split", 2: "k_flow", 3: "k_wide", 4: "k_pairs"}
+DTYPE = "u32+f32"       # integer recursion; f32 outputs by mantissa fill (one exact subtraction for [0,1))
 
 
 def kernel_hash() -> str:
@@ -197,7 +200,7 @@ def run_reference(args, rank, world):
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gnum/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE,
         "data": "synthetic", "config": {"workload": WORKLOAD_DESC[args.workload], "generators": len(ps)},
         "cpu_baseline": {"value": value, "unit": "Gnum/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Gnum/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -416,6 +419,7 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    pool.set_timing(args.steps)                          # events around each call's two launches
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -431,6 +435,8 @@ def main():
     torch.cuda.synchronize()
     t_host1 = time.perf_counter()
     launches = pool.launch_count() - launches0
+    jump_ms, gen_ms = pool.kernel_times(args.steps)
+    pool.set_timing(0)
     errs = pool.errors()                                 # shape / bounded-wait flags of the timed launches
     if errs:
         raise SystemExit(f"bench: kernel error flags {errs:#x} set during the timed steps; outputs invalid")
@@ -447,18 +453,19 @@ def main():
     peak, peak_kind = measured_peaks()
     state_bytes = sum(8 * p.N for p in ps)
     alg_bytes = 4 * total + state_bytes                  # per launch: outputs + state load/store
-    avg_launch = statistics.mean(launch_ms)
-    achieved = alg_bytes / (avg_launch * 1e-3) / 1e9
-    traffic = None                                       # ncu DRAM bytes, scaled to this launch
-    if os.path.exists(NCU_SUMMARY) and args.workload in ("c2", "c2s", "c2m"):
-        fields = {}
-        with open(NCU_SUMMARY) as f:
-            for ln in f:
-                if ":" in ln and ln.split(":", 1)[0].strip() in ("kernel_hash", "traffic_bytes_per_number"):
-                    k, v = ln.split(":", 1)
-                    fields[k.strip()] = v.strip().strip("`")
-        if fields.get("kernel_hash") == kernel_hash() and "traffic_bytes_per_number" in fields:
-            traffic = float(fields["traffic_bytes_per_number"]) * total
+    avg_launch = statistics.mean(launch_ms)              # whole step (jump + generation)
+    avg_gen = statistics.mean(gen_ms)                    # the generation launch alone
+    avg_jump = statistics.mean(jump_ms)
+    achieved = alg_bytes / (avg_gen * 1e-3) / 1e9
+    kname = FORM_KERNEL.get(cfg["form"], "k_generate")
+    traffic, traffic_src = None, None                    # ncu DRAM bytes, scaled to this launch
+    summary = os.path.join(ROOT, "profiles", f"{kname}_traffic.json")
+    if os.path.exists(summary) and args.workload in ("c2", "c2s", "c2m"):
+        with open(summary) as f:
+            tj = json.load(f)
+        if tj.get("kernel_hash") == kernel_hash():
+            traffic = float(tj["traffic_bytes_per_number"]) * total
+            traffic_src = os.path.relpath(summary, ROOT)
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -499,7 +506,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "Gnum/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC[args.workload],
                        "generators": len(wl.gens), "numbers_per_step": total,
                        "bytes_written_per_step": 4 * total,
@@ -508,9 +515,13 @@ def main():
             "hbm_write_gbs": 4 * numbers_all / world / (ms_total * 1e-3) / 1e9,
             "write_probe_gbs": write_probe_gbs,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_generate", "alg_bytes_per_launch": alg_bytes,
-                         "avg_launch_ms": avg_launch, "frac_of_write_probe": achieved / write_probe_gbs},
+                         "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                         "peak_kind": peak_kind, "kernel": kname, "alg_bytes_per_launch": alg_bytes,
+                         "avg_launch_ms": avg_gen, "timing": "CUDA events around the generation launch, "
+                         "recorded by the pool on the launching stream in every timed step",
+                         "frac_of_write_probe": achieved / write_probe_gbs},
+            "step_roofline": {"achieved": alg_bytes / (avg_launch * 1e-3) / 1e9, "avg_step_ms": avg_launch,
+                              "avg_jump_ms": avg_jump, "frac": alg_bytes / (avg_launch * 1e-3) / 1e9 / peak},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "kernel_hash": kernel_hash(),
         }

@@ -346,6 +346,24 @@ mtgp_status mtgp_pool_errors(mtgp_pool *p, uint32_t *flags);
  * the two jump-ahead kernels of calls that split work into pieces). */
 mtgp_status mtgp_pool_launch_count(const mtgp_pool *p, uint64_t *launches);
 
+/*
+ * Per-kernel timing, for measurement.  With entries > 0, each later
+ * mtgp_pool_generate call that launches work records three CUDA events on its
+ * stream: before its jump-ahead launch (Sec. 7), and before and after its
+ * generation launch, into a ring of `entries` records (created here, so that
+ * the timed calls create nothing).  entries = 0 turns it off.  Waits for the
+ * pool's queued work.
+ */
+mtgp_status mtgp_pool_set_timing(mtgp_pool *p, uint32_t entries);
+
+/*
+ * The device durations, in ms, of the last `count` recorded calls (oldest
+ * first): jump_ms[k] the jump-ahead launch (0 if the call had none), gen_ms[k]
+ * the generation launch.  Waits for those calls.  MTGP_EINVAL if fewer were
+ * recorded.
+ */
+mtgp_status mtgp_pool_kernel_times(mtgp_pool *p, uint32_t count, float *jump_ms, float *gen_ms);
+
 /* ---- jump-ahead (Sec. 7) ------------------------------------------------------
  *
  * Sec. 7 observes that one generator's stream can be produced by several

@@ -30,6 +30,8 @@ MAX_SLOTS_SPLIT = {128: 12, 256: 11, 512: 6, 1024: 3}
 MAX_SLOTS_FLOW = {128: 12, 256: 11, 512: 6, 1024: 8}
 # wide form: block size -> groups of 4 columns per thread
 MAX_SLOTS_WIDE = {96: 4, 128: 3, 192: 2}
+# pair form: block size -> slots of two adjacent columns per thread
+MAX_SLOTS_PAIRS = {32: 6, 128: 6}
 STATUS_NAMES = {0: "MTGP_OK", 1: "MTGP_EINVAL", 2: "MTGP_ENOMEM", 3: "MTGP_ECUDA",
                 4: "MTGP_ETIMEOUT", 5: "MTGP_EBUSY"}
 
@@ -105,6 +107,8 @@ _SIGS = {
     "mtgp_fill_probe": (ctypes.c_int, [_vp, _u64, _u32, _vp]),
     "mtgp_pool_errors": (ctypes.c_int, [_vp, _P(_u32)]),
     "mtgp_pool_launch_count": (ctypes.c_int, [_vp, _P(_u64)]),
+    "mtgp_pool_set_timing": (ctypes.c_int, [_vp, _u32]),
+    "mtgp_pool_kernel_times": (ctypes.c_int, [_vp, _u32, _P(ctypes.c_float), _P(ctypes.c_float)]),
     "mtgp_pool_jump": (ctypes.c_int, [_vp, _u32, _u64, _vp]),
     "mtgp_state_jump": (ctypes.c_int, [_vp, _u64, _vp]),
     "mtgp_pool_annihilator": (ctypes.c_int, [_vp, _u32, _P(_u64), _u32, _P(_u32), _vp]),

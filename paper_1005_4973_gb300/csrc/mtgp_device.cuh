@@ -79,7 +79,7 @@ __device__ __forceinline__ void round_sync()
 // stores.  x points at this thread's x_{rS+tid}, out at its output slot.
 // When QN = Q the last slot is the round's tail and only lanes with
 // last_lane set keep its result.
-template <int T, int Q, int QN, int DT>
+template <int T, int Q, int QN, int DT, bool CS = false>
 __device__ __forceinline__ void round_slots(const GenCtx &g, uint32_t *x, uint32_t (&prev)[Q],
                                             uint32_t *__restrict__ out, bool last_lane)
 {
@@ -96,7 +96,10 @@ __device__ __forceinline__ void round_slots(const GenCtx &g, uint32_t *x, uint32
 #pragma unroll
         for (int q = 0; q < QN; ++q) {
             const uint32_t t = b[q] ^ (a[q] & g.mask);
-            u[q] = t ^ (t << g.sh1) ^ (prev[q] >> g.sh2);
+            if constexpr (CS)                  // the shifts of Sec. 5, sh1 = 13, sh2 = 4, as constants
+                u[q] = t ^ (t << 13) ^ (prev[q] >> 4);
+            else
+                u[q] = t ^ (t << g.sh1) ^ (prev[q] >> g.sh2);
         }
 #pragma unroll
         for (int q = 0; q < QN; ++q)
@@ -130,25 +133,25 @@ __device__ __forceinline__ void round_slots(const GenCtx &g, uint32_t *x, uint32
 //     columns run the tail slot -- measured faster when many blocks share
 //     each SM.  The two are separate kernels: one kernel with a run-time
 //     choice measured slower than either.
-template <int T, int Q, int DT, bool IL>
+template <int T, int Q, int DT, bool IL, bool CS = false>
 __device__ __forceinline__ void round_fast(const GenCtx &g, uint32_t *x, uint32_t (&prev)[Q],
                                            uint32_t *__restrict__ out, bool tail_warp, bool tail_lane)
 {
     if constexpr (IL) {
         if (tail_warp)
-            round_slots<T, Q, Q, DT>(g, x, prev, out, tail_lane);
+            round_slots<T, Q, Q, DT, CS>(g, x, prev, out, tail_lane);
         else
-            round_slots<T, Q, Q - 1, DT>(g, x, prev, out, true);
+            round_slots<T, Q, Q - 1, DT, CS>(g, x, prev, out, true);
         return;
     }
-    round_slots<T, Q, Q - 1, DT>(g, x, prev, out, true);
+    round_slots<T, Q, Q - 1, DT, CS>(g, x, prev, out, true);
     if (tail_warp) {
         constexpr int q = Q - 1;
         const uint32_t *xt_p = x + (g.M - 1u);
         uint32_t *xn_p = x + g.N;
         const uint32_t a0 = x[q * T], b0 = x[q * T + 1], c0 = xt_p[q * T];
         const uint32_t t = b0 ^ (a0 & g.mask);
-        const uint32_t uu = t ^ (t << g.sh1) ^ (prev[q] >> g.sh2);
+        const uint32_t uu = CS ? t ^ (t << 13) ^ (prev[q] >> 4) : t ^ (t << g.sh1) ^ (prev[q] >> g.sh2);
         const uint32_t xn = uu ^ __shfl_sync(0xffffffffu, g.rec_r, (int)uu, 16);
         uint32_t s = c0 ^ (c0 >> 16);
         s ^= s >> 8;
@@ -162,7 +165,7 @@ __device__ __forceinline__ void round_fast(const GenCtx &g, uint32_t *x, uint32_
 }
 
 // Runs `rounds` full rounds inside one blocked segment of dtype DT.
-template <int T, int Q, int DT, bool IL>
+template <int T, int Q, int DT, bool IL, bool CS = false>
 __device__ __forceinline__ void run_fast(const GenCtx &g, uint32_t *buf, uint32_t B, uint32_t &rel,
                                          uint32_t (&prev)[Q], uint32_t rounds, uint32_t *out)
 {
@@ -185,7 +188,7 @@ __device__ __forceinline__ void run_fast(const GenCtx &g, uint32_t *buf, uint32_
             }
 #pragma unroll
             for (uint32_t k = 0; k < U; ++k) {
-                round_fast<T, Q, DT, IL>(g, buf + rel + k * g.S + tid, prev, out + k * g.S, tail_warp, tail_lane);
+                round_fast<T, Q, DT, IL, CS>(g, buf + rel + k * g.S + tid, prev, out + k * g.S, tail_warp, tail_lane);
                 round_sync<T>();
             }
             rel += U * g.S;
@@ -198,7 +201,7 @@ __device__ __forceinline__ void run_fast(const GenCtx &g, uint32_t *buf, uint32_
             round_sync<T>();
             rel = 0;
         }
-        round_fast<T, Q, DT, IL>(g, buf + rel + tid, prev, out, tail_warp, tail_lane);
+        round_fast<T, Q, DT, IL, CS>(g, buf + rel + tid, prev, out, tail_warp, tail_lane);
         round_sync<T>();
         rel += g.S;
         out += g.S;
@@ -281,6 +284,10 @@ __device__ __forceinline__ void run_item(const GenCtx g, uint32_t *buf, uint32_t
 #pragma unroll
     for (int q = 0; q < Q; ++q)                          // x_{c+M}, c = column
         prev[q] = (q * T + tid < g.S) ? buf[q * T + tid + g.M] : 0u;
+    // parameter sets with the Sec. 5 shifts run full rounds with the shifts as
+    // constants (slot counts of MTGPs 11213, 23209, 44497 in 128-thread blocks)
+    constexpr bool kCS = T == 128 && (Q == 3 || Q == 6 || Q == 11);
+    const bool cs = kCS && g.sh1 == 13u && g.sh2 == 4u;
     uint32_t rel = 0, si = 0;
     uint64_t k0 = 0, seg_start = 0, seg_end = segs[0].n;
     while (k0 < w.total) {
@@ -294,12 +301,21 @@ __device__ __forceinline__ void run_item(const GenCtx g, uint32_t *buf, uint32_t
         if (full > 0 && sg.chunk_log2 == kBlocked) {
             uint32_t *out = out_base + sg.out_off + (k0 - seg_start);
             const uint32_t rounds = (uint32_t)min(full, (uint64_t)0x7FFFFFFFu);
-            if (sg.dtype == 0u)
-                run_fast<T, Q, 0, IL>(g, buf, B, rel, prev, rounds, out);
-            else if (sg.dtype == 1u)
-                run_fast<T, Q, 1, IL>(g, buf, B, rel, prev, rounds, out);
-            else
-                run_fast<T, Q, 2, IL>(g, buf, B, rel, prev, rounds, out);
+            if (cs) {
+                if (sg.dtype == 0u)
+                    run_fast<T, Q, 0, IL, kCS>(g, buf, B, rel, prev, rounds, out);
+                else if (sg.dtype == 1u)
+                    run_fast<T, Q, 1, IL, kCS>(g, buf, B, rel, prev, rounds, out);
+                else
+                    run_fast<T, Q, 2, IL, kCS>(g, buf, B, rel, prev, rounds, out);
+            } else {
+                if (sg.dtype == 0u)
+                    run_fast<T, Q, 0, IL>(g, buf, B, rel, prev, rounds, out);
+                else if (sg.dtype == 1u)
+                    run_fast<T, Q, 1, IL>(g, buf, B, rel, prev, rounds, out);
+                else
+                    run_fast<T, Q, 2, IL>(g, buf, B, rel, prev, rounds, out);
+            }
             k0 += (uint64_t)rounds * g.S;
         } else {
             maybe_compact<T, Q>(g, buf, B, rel);

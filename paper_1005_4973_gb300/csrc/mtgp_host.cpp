@@ -182,6 +182,12 @@ struct mtgp_pool {
     // graphs whose work lists may hold jump jobs, which point at polynomials
     // in jc: emptied before those polynomials are freed
     std::vector<mtgp_graph *> jump_graphs;
+    // per-kernel timing (mtgp_pool_set_timing): a ring of timing_n entries of
+    // three events (before the jump launch, before and after the generation
+    // launch) recorded by the last calls
+    std::vector<cudaEvent_t> tev;
+    std::vector<uint8_t> tjump;
+    uint32_t timing_n = 0, timing_next = 0, timing_count = 0;
 };
 
 struct mtgp_state {
@@ -240,7 +246,8 @@ constexpr uint64_t kSeqCap = 256ull << 20;           // walk scratch words per l
 
 mtgp_status check_config(const mtgp_config &c)
 {
-    if (c.form > 3u) return fail(MTGP_EINVAL, "form must be 0 (plain), 1 (split), 2 (flow) or 3 (wide)");
+    if (c.form > 4u)
+        return fail(MTGP_EINVAL, "form must be 0 (plain), 1 (split), 2 (flow), 3 (wide) or 4 (pairs)");
     if (!threads_supported(c.threads, c.form))
         return fail(MTGP_EINVAL, "no kernel of form %u with %u threads per block", c.form, c.threads);
     if (c.persistent > 1u) return fail(MTGP_EINVAL, "persistent must be 0 or 1");
@@ -453,7 +460,9 @@ mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_
         smax = std::max(smax, g.N - g.M);
     }
     if (c.form == 3u) return launch_shape_wide(p, c, gens, n, items, nmax, smax, qmax_out, B_out);
-    const uint32_t owners = c.form ? c.threads / 2u : c.threads;   // threads owning columns
+    // columns a slot covers: one per thread (plain), one per thread of the
+    // recursion half (split, flow), two per thread (pairs)
+    const uint32_t owners = c.form == 4u ? 2u * c.threads : c.form ? c.threads / 2u : c.threads;
     const uint32_t qmax = kernel_slots(c.threads, c.form, (smax + owners - 1u) / owners);
     if (!qmax)
         return fail(MTGP_EINVAL, "no compiled kernel runs rounds of %u words with %u threads (form %u)", smax,
@@ -486,6 +495,15 @@ mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_
         B = std::max(B, std::min(need + smax, 57344u));
         B = std::max(B, need);
     }
+    if (c.form == 4u && !c.buffer_words) {
+        // two halves of H words, H = 16 (mod 32): the copies between the
+        // halves stay free of bank conflicts
+        uint32_t H = B / 2u;
+        H = H < 16u ? 16u : ((H - 16u) & ~31u) + 16u;
+        if (2u * H < need) H += 32u;
+        B = 2u * H;
+    }
+    if (c.form == 4u) B &= ~1u;                               // the kernel uses 2 floor(B / 2) words
     if (B < need) return fail(MTGP_EINVAL, "buffer_words %u below the minimum %u for this launch", B, need);
     if (B > 57344u) return fail(MTGP_EINVAL, "state too large for shared memory (%u words)", B);
     *qmax_out = qmax;
@@ -689,6 +707,14 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
        "upload work list");
     CU(cudaEventRecord(p->ev_upload, s), "cudaEventRecord");
     p->upload_pending = true;
+    cudaEvent_t *tev = nullptr;                       // this call's timing entry
+    if (p->timing_n) {
+        tev = &p->tev[3u * p->timing_next];
+        p->tjump[p->timing_next] = plan.jobs.empty() ? 0u : 1u;
+        p->timing_next = (p->timing_next + 1u) % p->timing_n;
+        p->timing_count = std::min(p->timing_count + 1u, p->timing_n);
+        CU(cudaEventRecord(tev[0], s), "cudaEventRecord");
+    }
     if (!plan.jobs.empty()) {   // start states of the pieces (Sec. 7)
         const DevJump *jobs = (const DevJump *)((char *)p->d_work + wbytes + sbytes);
         const uint32_t nj = (uint32_t)plan.jobs.size();
@@ -734,7 +760,9 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     a.persistent = persistent ? 1u : 0u;
     a.jstate = p->d_jstate;
     a.interleave = interleave ? 1u : 0u;
+    if (tev) CU(cudaEventRecord(tev[1], s), "cudaEventRecord");
     CU(launch_generate(a, c.threads, c.form, qmax, grid, s), "generate kernel launch");
+    if (tev) CU(cudaEventRecord(tev[2], s), "cudaEventRecord");
     p->launches += 1u;
     CU(cudaEventRecord(p->ev_done, s), "cudaEventRecord");
     p->last_stream = s;
@@ -1129,6 +1157,7 @@ void mtgp_pool_destroy(mtgp_pool *p)
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->ev_done) cudaEventDestroy(p->ev_done);
     if (p->ev_upload) cudaEventDestroy(p->ev_upload);
+    for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
     delete p;
     (void)cudaGetLastError();      // the statuses above are ignored: leave none behind
 }
@@ -1507,6 +1536,45 @@ mtgp_status mtgp_pool_launch_count(const mtgp_pool *p, uint64_t *launches)
 {
     if (!p || !launches) return fail(MTGP_EINVAL, "NULL argument");
     *launches = p->launches;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_set_timing(mtgp_pool *p, uint32_t entries)
+{
+    return guarded([&]() -> mtgp_status {
+        if (!p) return fail(MTGP_EINVAL, "NULL pool");
+        if (entries > 65536u) return fail(MTGP_EINVAL, "at most 65536 timing entries");
+        mtgp_status st = pool_sync(p);
+        if (st != MTGP_OK) return st;
+        for (cudaEvent_t e : p->tev) CU(cudaEventDestroy(e), "cudaEventDestroy");
+        p->tev.clear();
+        p->tjump.assign(entries, 0u);
+        p->timing_n = p->timing_next = p->timing_count = 0;
+        for (uint32_t i = 0; i < 3u * entries; ++i) {
+            cudaEvent_t e = nullptr;
+            CU(cudaEventCreate(&e), "cudaEventCreate");
+            p->tev.push_back(e);
+        }
+        p->timing_n = entries;
+        return MTGP_OK;
+    });
+}
+
+mtgp_status mtgp_pool_kernel_times(mtgp_pool *p, uint32_t count, float *jump_ms, float *gen_ms)
+{
+    if (!p || (count && (!jump_ms || !gen_ms))) return fail(MTGP_EINVAL, "NULL argument");
+    if (count > p->timing_count)
+        return fail(MTGP_EINVAL, "%u timed calls requested, %u recorded", count, p->timing_count);
+    for (uint32_t k = 0; k < count; ++k) {      // oldest first
+        const uint32_t e = (p->timing_next + p->timing_n - count + k) % p->timing_n;
+        cudaEvent_t *t = &p->tev[3u * e];
+        CU(cudaEventSynchronize(t[2]), "cudaEventSynchronize");
+        float a = 0.f, b = 0.f;
+        if (p->tjump[e]) CU(cudaEventElapsedTime(&a, t[0], t[1]), "cudaEventElapsedTime");
+        CU(cudaEventElapsedTime(&b, t[1], t[2]), "cudaEventElapsedTime");
+        jump_ms[k] = a;
+        gen_ms[k] = b;
+    }
     return MTGP_OK;
 }
 

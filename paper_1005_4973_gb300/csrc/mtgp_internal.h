@@ -71,6 +71,13 @@ GenKernel split_kernel_rt512(uint32_t qmax);
 // adjacent columns of a round; T in {96, 128, 192}, QW in {1, 2, 4},
 // {1, 2, 3}, {1, 2}.  Blocked layouts only.
 GenKernel wide_kernel(uint32_t threads, uint32_t qw);
+// Pair-form kernels (form 4): 128 threads per block, each owning two adjacent
+// columns per slot; QMAX pair slots (rounds of up to 256 QMAX words), QMAX in
+// {2, 3, 6}.
+GenKernel pair_kernel_t32_q6();   // one warp per block, rounds of up to 384 words
+GenKernel pair_kernel_t128_q2();
+GenKernel pair_kernel_t128_q3();
+GenKernel pair_kernel_t128_q6();
 // Flow-form kernels: blocks of 2 W warps (W recursion + W output warps).
 GenKernel flow_kernel_w2(uint32_t cmax);
 GenKernel flow_kernel_w4(uint32_t cmax);
@@ -91,7 +98,8 @@ cudaError_t raise_smem_limit(const void *kernel, size_t dyn_bytes);
 
 bool threads_supported(uint32_t threads, uint32_t form);
 // Smallest compiled QMAX >= nq for this block size and form, 0 if none.
-// In the split and flow forms a thread owns ceil(S / (threads / 2)) columns.
+// In the split and flow forms a thread owns ceil(S / (threads / 2)) columns;
+// in the pair form ceil(S / (2 threads)) pairs of columns.
 uint32_t kernel_slots(uint32_t threads, uint32_t form, uint32_t nq);
 cudaError_t launch_seed(DevGen *gens, uint32_t *state, const uint32_t *gen_ids,
                         const uint64_t *seeds, uint32_t first, uint32_t count, cudaStream_t s);

@@ -62,6 +62,18 @@ GenKernel pick(uint32_t threads, uint32_t form, uint32_t qmax, bool interleave =
         if (k) return k;
     }
     if (form == 3u) return wide_kernel(threads, qmax);
+    if (form == 4u) {
+        if (threads == 32u) return qmax == 6u ? pair_kernel_t32_q6() : nullptr;
+        if (threads == 128u) {
+            switch (qmax) {
+            case 2: return pair_kernel_t128_q2();
+            case 3: return pair_kernel_t128_q3();
+            case 6: return pair_kernel_t128_q6();
+            default: return nullptr;
+            }
+        }
+        return nullptr;
+    }
     if (form == 2u) {
         switch (threads) {
         case 128: return flow_kernel_w2(qmax);

@@ -215,6 +215,17 @@ class Pool:
         L.check(L.LIB.mtgp_pool_launch_count(self.handle, ctypes.byref(v)))
         return v.value
 
+    def set_timing(self, entries: int) -> None:
+        """Record CUDA events around the jump and generation launches of the next calls."""
+        L.check(L.LIB.mtgp_pool_set_timing(self.handle, entries))
+
+    def kernel_times(self, count: int):
+        """(jump_ms, gen_ms) lists of the last `count` recorded calls, oldest first."""
+        a = (ctypes.c_float * max(count, 1))()
+        b = (ctypes.c_float * max(count, 1))()
+        L.check(L.LIB.mtgp_pool_kernel_times(self.handle, count, a, b))
+        return list(a)[:count], list(b)[:count]
+
     # -- jump-ahead (Sec. 7) ----------------------------------------------------
     def jump(self, i: int, steps: int, stream=None) -> None:
         L.check(L.LIB.mtgp_pool_jump(self.handle, i, steps, L.stream_handle(stream)))

@@ -15,7 +15,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FORMS = [dict(threads=128, form=0), dict(threads=256, form=1), dict(threads=256, form=2),
-         dict(threads=128, form=0, persistent=1, blocks_per_sm=1)]
+         dict(threads=128, form=0, persistent=1, blocks_per_sm=1), dict(threads=128, form=4),
+         dict(threads=128, form=4, persistent=1, blocks_per_sm=1)]
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -87,8 +87,8 @@ def _round_size(spec):
 
 
 FORMS = [(32, 0), (64, 0), (128, 0), (256, 0), (512, 0), (128, 1), (256, 1), (512, 1), (1024, 1),
-         (128, 2), (256, 2), (512, 2), (1024, 2)]
-FORM_ID = lambda f: f"{f[0]}{'psf'[f[1]]}"
+         (128, 2), (256, 2), (512, 2), (1024, 2), (128, 4)]
+FORM_ID = lambda f: f"{f[0]}{'psfwq'[f[1]]}"
 
 
 def _need(p, threads, fm):
@@ -100,12 +100,15 @@ def _need(p, threads, fm):
 
 
 def _owners(threads, form):
-    return threads // 2 if form else threads
+    """Columns one slot covers: a column per thread (plain), per thread of the
+    recursion half (split, flow), two per thread (pairs)."""
+    return 2 * threads if form == 4 else threads // 2 if form else threads
 
 
 def _max_slots(threads, form):
-    from paper_1005_4973_gb300._lib import MAX_SLOTS, MAX_SLOTS_FLOW, MAX_SLOTS_SPLIT
-    return (MAX_SLOTS_SPLIT if form == 1 else MAX_SLOTS_FLOW if form == 2 else MAX_SLOTS)[threads]
+    from paper_1005_4973_gb300._lib import MAX_SLOTS, MAX_SLOTS_FLOW, MAX_SLOTS_PAIRS, MAX_SLOTS_SPLIT
+    return (MAX_SLOTS_SPLIT if form == 1 else MAX_SLOTS_FLOW if form == 2 else MAX_SLOTS_PAIRS if form == 4
+            else MAX_SLOTS)[threads]
 
 
 @pytest.mark.parametrize("form", FORMS, ids=FORM_ID)
@@ -171,7 +174,7 @@ def test_flow_partial_last_round_with_idle_warps(tail):
 
 
 @pytest.mark.parametrize("extra", [0, 1, 7, 300, 2000])
-@pytest.mark.parametrize("form", [(128, 0), (256, 1), (256, 2), (1024, 2)], ids=FORM_ID)
+@pytest.mark.parametrize("form", [(128, 0), (256, 1), (256, 2), (1024, 2), (128, 4)], ids=FORM_ID)
 def test_small_buffers_force_compaction(extra, form):
     # buffer_words at (or just above) its minimum: compaction every round or
     # few rounds (split form: every compaction drains the hand-off ring; flow
@@ -201,7 +204,8 @@ def test_too_small_buffer_rejected():
         big.generate([(0, 0, 16, 0)], out)
 
 
-def test_random_shift_sets():
+@pytest.mark.parametrize("form", [(128, 0), (128, 4)], ids=FORM_ID)
+def test_random_shift_sets(form):
     # sh1, sh2 over [1, 31] exercise every shift path; the shift values are
     # recipe inputs (numpy RNG) applied to each side's own drawn set.
     import paper_1005_4973_gb300 as M
@@ -217,6 +221,7 @@ def test_random_shift_sets():
         ops.append(O.params_from_fields(mexp, o.pos, int(shifts[s, 0]), int(shifts[s, 1]), s, list(o.R), list(o.T)))
         ps.append(lp)
     pool = M.Pool(ps, list(range(8)), [7] * 8)
+    pool.set_config(threads=form[0], form=form[1])
     reqs = [(i, i % 3, 7777, i * 7777) for i in range(8)]
     out = torch.zeros(8 * 7777, dtype=torch.int32, device="cuda")
     pool.generate(reqs, out)

@@ -31,7 +31,7 @@ def _oracle_streams(gens, per_gen):
     return res
 
 
-@pytest.mark.parametrize("form", [(128, 0), (256, 1), (256, 2)])
+@pytest.mark.parametrize("form", [(128, 0), (256, 1), (256, 2), (128, 4)])
 def test_graph_replays_with_changing_work(form):
     """One captured launch, replayed with new work lists (and twice with the
     same list, which continues the streams); every replay's output matches the
@@ -217,7 +217,7 @@ def _random_requests(seed, count, max_len):
             for _ in range(count)]
 
 
-@pytest.mark.parametrize("form", [(128, 0), (256, 2)])
+@pytest.mark.parametrize("form", [(128, 0), (256, 2), (128, 4)])
 def test_server_mix_equals_alone(form):
     """Requests of 12 generators arrive while others are being generated; every
     result equals the oracle stream of its generator's requests in order."""

@@ -179,9 +179,9 @@ mtgp_status mtgp_params_validate(const mtgp_params *p);
  * in *found_seed, t + 1 in *tries, and, if charpoly is not NULL, phi (bit j of
  * word j/64 = coefficient of x^j; charpoly_words >= mexp / 64 + 1).
  * threads = 0 uses every host core.  MTGP_EINVAL if none of max_tries
- * candidates qualifies.  The tempering table is drawn, not searched (the
- * k(v) search of Sec. 5 is not implemented).  About a minute of 16 cores for
- * mexp 11213; the cost grows roughly as mexp^3.
+ * candidates qualifies.  The tempering table of the result is the drawn one;
+ * mtgp_params_temper_search replaces it by the search of Sec. 5.  6-9 s of 16
+ * cores for mexp 11213; the cost grows roughly as mexp^3.
  */
 mtgp_status mtgp_params_search(uint32_t mexp, uint64_t seed0, uint32_t id, uint64_t max_tries, uint32_t threads,
                                mtgp_params *out, uint64_t *found_seed, uint64_t *tries, uint64_t *charpoly,
@@ -192,27 +192,55 @@ mtgp_status mtgp_params_search(uint32_t mexp, uint64_t seed0, uint32_t id, uint6
  * 32 of the tempered uint32 output -- the largest k such that the v most
  * significant bits of k consecutive outputs are equidistributed over a
  * period -- to kv[v - 1], and the total dimension defect sum_v (floor(mexp /
- * v) - k(v)) to *delta (if not NULL).  For an F2-linear generator of period
- * 2^mexp - 1, k(v) is the largest k for which the map from states to those k
- * v bits is onto; the library takes the states F^j s (j < mexp) of one
- * nonzero state s as the basis and row-reduces, one host thread per v.  The
- * result is meaningful for full-period sets (mtgp_params_search); for others
- * it describes the orbit of that state.  Seconds for mexp 11213 on 16 cores,
- * growing as mexp^3.
+ * v) - k(v)) to *delta (if not NULL).  For a full-period set (characteristic
+ * polynomial P of degree mexp, irreducible) k(v) is the least max-degree of
+ * the nonzero vectors (f_1 .. f_v) over F2[t] with sum_j f_j h_j = 0 mod P,
+ * h_j / P the generating function of output bit 32 - j: a lattice that the
+ * library reduces to weak Popov form, one bit at a time (Sec. 5 uses a
+ * lattice method too); a fraction of a second for mexp 11213.  Other sets
+ * (P of lower degree: k(v) then describes the orbit of one state) fall back
+ * to row reduction of the states F^j s, one host thread per v (seconds).
  */
 mtgp_status mtgp_params_equidistribution(const mtgp_params *p, uint32_t threads, uint32_t *kv, uint32_t *delta);
 
+/* The same for the v LEAST significant bits (k'(v) of Sec. 5: bits 0 .. v-1). */
+mtgp_status mtgp_params_equidistribution_lsb(const mtgp_params *p, uint32_t threads, uint32_t *kv,
+                                             uint32_t *delta);
+
 /*
- * Tempering search (Sec. 5: MTGPDC searches a tempering set once the
- * recursion set is found; the paper does not say how): candidate 0 is the
- * input's tmp_tbl, candidate t = 1 .. tries the table of four random rows
- * (SplitMix64 from seed + t, Sec. 3.7 table convention).  *out = the input
- * with the table of the smallest total dimension defect (earliest on ties),
- * that defect to *delta (if not NULL).  Each candidate costs one
- * mtgp_params_equidistribution.  For full-period sets.
+ * Tempering search of Sec. 5 for a full-period set *in (its tmp_tbl is
+ * ignored): the four tempering rows start at zero; for row 0, 1, 2, 3 in
+ * turn, the 23 MSBs are set in windows of bits j .. e-1 counted from the MSB
+ * (j = 0, 5, 10, 15, 20; e = min(j + 5, 23)), each to the pattern with the
+ * least d(1) + .. + d(e) (every pattern of the window tried, the smallest
+ * pattern value on ties); then, row by row, the 9 LSBs in windows of bits
+ * j .. e-1 counted from the LSB (j = 0, 5; e = min(j + 5, 9)) against the
+ * defects d'(1) + .. + d'(e) of the v least significant bits.  *out = *in
+ * with the table of the rows found (bit 3 of the index selects row 0), its
+ * total MSB defect to *delta (if not NULL).  threads = 0 uses every host
+ * core (the patterns of a window run in parallel).  MTGP_EINVAL for a set
+ * that is not of full period.
  */
-mtgp_status mtgp_params_temper_search(const mtgp_params *in, uint64_t seed, uint32_t tries, uint32_t threads,
-                                      mtgp_params *out, uint32_t *delta);
+mtgp_status mtgp_params_temper_search(const mtgp_params *in, uint32_t threads, mtgp_params *out, uint32_t *delta);
+
+/*
+ * Table 1 style report of a set (Sec. 3.8): one line per v = 1 .. 32 with
+ * v, k(v), d(v) = floor(mexp / v) - k(v) and r(v) = 100 d(v) / (k(v) + d(v))
+ * in percent, then "total dimension defect <sum of d(v)>".  NUL-terminated
+ * text into buf (len bytes; MTGP_EINVAL if too small, 2 KiB suffice).
+ */
+mtgp_status mtgp_params_report(const mtgp_params *p, uint32_t threads, char *buf, size_t len);
+
+/*
+ * MTGPDC record of a searched set (Sec. 5): comma-separated mexp, N, pos,
+ * sh1, sh2, id, the 16 rec_tbl and 16 tmp_tbl entries (8 hexadecimal
+ * digits each), the SHA-1 digest of the characteristic polynomial (of its
+ * coefficients written as '0' / '1' characters from x^0 up to x^mexp), its
+ * number of nonzero terms, and the total dimension defect.  charpoly: bit i
+ * of word i / 64 = coefficient of x^i (as mtgp_params_search returns it).
+ */
+mtgp_status mtgp_params_record(const mtgp_params *p, const uint64_t *charpoly, uint32_t charpoly_words,
+                               uint32_t threads, char *buf, size_t len);
 
 /* ---- single generator (Sec. 8 host/kernel flow) --------------------------- */
 

@@ -284,6 +284,54 @@ def mt19937_outputs_init_genrand(seed: int, n: int) -> np.ndarray:
     return out
 
 
+def reverse_bits(words: np.ndarray) -> np.ndarray:
+    """Each 32-bit word with its bit order reversed (bit b to bit 31 - b)."""
+    words = np.asarray(words, dtype=np.uint32)
+    out = np.zeros_like(words)
+    for b in range(32):
+        out |= ((words >> np.uint32(b)) & np.uint32(1)) << np.uint32(31 - b)
+    return out
+
+
+def temper_search_sec5(op: OrcParams) -> list[int]:
+    """The tempering-parameter search of Sec. 5, restated step by step with
+    the row-reduction k(v) above: the four tempering rows start at zero; row
+    by row, the 23 MSBs are fixed in windows of bits j .. e-1 counted from the
+    MSB (j = 0, 5, 10, 15, 20; e = min(j + 5, 23)), each to the pattern with
+    the least d(1) + ... + d(e); then, row by row, the 9 LSBs in windows of
+    bits j .. e-1 counted from the LSB (j = 0, 5; e = min(j + 5, 9)) against
+    d'(1) + ... + d'(e) of the v least significant bits.  Every pattern of a
+    window is tried in increasing order and the first least sum kept.
+    Returns the four rows (row 0 first).  Full-period sets only."""
+    p = op.mexp
+    start = seed_state(op, 1, 2)
+    n = 2 * p + 64
+
+    def defects(rows, lsb, e):
+        q = params_from_fields(op.mexp, op.pos, op.sh1, op.sh2, op.id, list(op.R), rows)
+        out = generate(q, start.copy(), n, U32)
+        k = kv(reverse_bits(out) if lsb else out, p, vmax=e)
+        return sum(p // v - int(k[v - 1]) for v in range(1, e + 1))
+
+    rows = [0, 0, 0, 0]
+    for lsb, top in ((False, 23), (True, 9)):
+        for i in range(4):
+            for j in range(0, top, 5):
+                e = min(j + 5, top)
+                w = e - j
+                shift = j if lsb else 32 - e
+                mask = ((1 << w) - 1) << shift
+                best = None
+                for pat in range(1 << w):
+                    r = list(rows)
+                    r[i] = (r[i] & ~mask & 0xFFFFFFFF) | (pat << shift)
+                    d = defects(r, lsb, e)
+                    if best is None or d < best[0]:
+                        best = (d, r)
+                rows = best[1]
+    return rows
+
+
 def dimension_defects(k: np.ndarray, p: int) -> np.ndarray:
     """d(v) = floor(p / v) - k(v) (Sec. 3.4)."""
     v = np.arange(1, k.size + 1)

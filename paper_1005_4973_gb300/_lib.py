@@ -31,7 +31,7 @@ MAX_SLOTS_FLOW = {128: 12, 256: 11, 512: 6, 1024: 8}
 # wide form: block size -> groups of 4 columns per thread
 MAX_SLOTS_WIDE = {96: 4, 128: 3, 192: 2}
 # pair form: block size -> slots of two adjacent columns per thread
-MAX_SLOTS_PAIRS = {32: 6, 128: 6}
+MAX_SLOTS_PAIRS = {128: 6}
 STATUS_NAMES = {0: "MTGP_OK", 1: "MTGP_EINVAL", 2: "MTGP_ENOMEM", 3: "MTGP_ECUDA",
                 4: "MTGP_ETIMEOUT", 5: "MTGP_EBUSY"}
 
@@ -115,7 +115,10 @@ _SIGS = {
     "mtgp_params_search": (ctypes.c_int, [_u32, _u64, _u32, _u64, _u32, _P(mtgp_params), _P(_u64), _P(_u64),
                                           _P(_u64), _u32]),
     "mtgp_params_equidistribution": (ctypes.c_int, [_P(mtgp_params), _u32, _P(_u32), _P(_u32)]),
-    "mtgp_params_temper_search": (ctypes.c_int, [_P(mtgp_params), _u64, _u32, _u32, _P(mtgp_params), _P(_u32)]),
+    "mtgp_params_equidistribution_lsb": (ctypes.c_int, [_P(mtgp_params), _u32, _P(_u32), _P(_u32)]),
+    "mtgp_params_temper_search": (ctypes.c_int, [_P(mtgp_params), _u32, _P(mtgp_params), _P(_u32)]),
+    "mtgp_params_report": (ctypes.c_int, [_P(mtgp_params), _u32, ctypes.c_char_p, _sz]),
+    "mtgp_params_record": (ctypes.c_int, [_P(mtgp_params), _P(_u64), _u32, _u32, ctypes.c_char_p, _sz]),
     "mtgp_f2_minpoly": (ctypes.c_int, [_P(_u64), _u64, _P(_u64), _u32, _P(ctypes.c_int64)]),
     "mtgp_f2_mulmod": (ctypes.c_int, [_P(_u64), _u32, _P(_u64), _u32, _P(_u64), _u32, _P(_u64), _u32,
                                       _P(ctypes.c_int64)]),

@@ -74,7 +74,6 @@ GenKernel wide_kernel(uint32_t threads, uint32_t qw);
 // Pair-form kernels (form 4): 128 threads per block, each owning two adjacent
 // columns per slot; QMAX pair slots (rounds of up to 256 QMAX words), QMAX in
 // {2, 3, 6}.
-GenKernel pair_kernel_t32_q6();   // one warp per block, rounds of up to 384 words
 GenKernel pair_kernel_t128_q2();
 GenKernel pair_kernel_t128_q3();
 GenKernel pair_kernel_t128_q6();

@@ -63,7 +63,6 @@ GenKernel pick(uint32_t threads, uint32_t form, uint32_t qmax, bool interleave =
     }
     if (form == 3u) return wide_kernel(threads, qmax);
     if (form == 4u) {
-        if (threads == 32u) return qmax == 6u ? pair_kernel_t32_q6() : nullptr;
         if (threads == 128u) {
             switch (qmax) {
             case 2: return pair_kernel_t128_q2();

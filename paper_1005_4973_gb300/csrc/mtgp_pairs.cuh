@@ -345,14 +345,13 @@ __device__ __forceinline__ void pair_run_fast_s(const PairCtx &g, uint32_t *buf,
 }
 
 // Slot counts with the specialised paired-round loops (the rounds of
-// MTGPs 11213, 23209 and 44497 in 128-thread blocks, of MTGP11213 in one-warp
-// blocks); other counts, and parameter sets with other shifts than sh1 = 13,
-// sh2 = 4, run single rounds of the one run-time path (same outputs; it
-// bounds the kernel's code size).
+// MTGPs 11213, 23209 and 44497 in 128-thread blocks); other counts, and
+// parameter sets with other shifts than sh1 = 13, sh2 = 4, run single rounds
+// of the one run-time path (same outputs; it bounds the kernel's code size).
 template <int T, int Q>
 __host__ __device__ constexpr bool pair_fast_slots()
 {
-    return T == 32 ? (Q == 5 || Q == 6) : (Q == 2 || Q == 3 || Q == 6);
+    return T == 128 && (Q == 2 || Q == 3 || Q == 6);
 }
 
 // `rounds` full rounds inside one blocked segment of dtype DT, one at a time.

@@ -44,41 +44,38 @@ def mtgp_params_equidistribution(p: mtgp_params, threads: int = 0):
     return np.array(list(kv), dtype=np.int64), delta.value
 
 
-def mtgp_params_temper_search(p: mtgp_params, seed: int, tries: int, threads: int = 0):
-    """Tempering search (Sec. 5): returns (params with the best table, its total defect)."""
+def mtgp_params_equidistribution_lsb(p: mtgp_params, threads: int = 0):
+    """k'(v) for v = 1..32 (the v least significant bits) and their total defect."""
+    kv = (ctypes.c_uint32 * 32)()
+    delta = ctypes.c_uint32()
+    L.check(L.LIB.mtgp_params_equidistribution_lsb(ctypes.byref(p), threads, kv, ctypes.byref(delta)))
+    return np.array(list(kv), dtype=np.int64), delta.value
+
+
+def mtgp_params_temper_search(p: mtgp_params, threads: int = 0):
+    """Tempering search of Sec. 5: returns (params with the table found, its total defect)."""
     out = mtgp_params()
     delta = ctypes.c_uint32()
-    L.check(L.LIB.mtgp_params_temper_search(ctypes.byref(p), seed, tries, threads, ctypes.byref(out),
-                                            ctypes.byref(delta)))
+    L.check(L.LIB.mtgp_params_temper_search(ctypes.byref(p), threads, ctypes.byref(out), ctypes.byref(delta)))
     return out, delta.value
 
 
-def equidistribution_table(p: mtgp_params, kv) -> str:
-    """Table 1 style report (Sec. 3.8): v, k(v), d(v) and the defect ratio
-    r(v) = 100 d(v) / (k(v) + d(v)) for v = 1..32, and the total defect."""
-    lines = ["   v     k(v)   d(v)   r(v)%"]
-    total = 0
-    for v in range(1, 33):
-        k = int(kv[v - 1])
-        d = p.mexp // v - k
-        total += d
-        lines.append(f"{v:4d} {k:8d} {d:6d} {100.0 * d / (k + d):7.2f}")
-    lines.append(f"total dimension defect {total}")
-    return "\n".join(lines)
+def mtgp_params_report(p: mtgp_params, threads: int = 0) -> str:
+    """Table 1 style report (Sec. 3.8): v, k(v), d(v), r(v) and the total defect."""
+    buf = ctypes.create_string_buffer(4096)
+    L.check(L.LIB.mtgp_params_report(ctypes.byref(p), threads, buf, len(buf)))
+    return buf.value.decode()
 
 
-def mtgpdc_record(p: mtgp_params, charpoly) -> str:
-    """One comma-separated record of a searched set, with the additional data
-    Sec. 5 lists: SHA1 of the characteristic polynomial (its coefficients as
-    a string of '0'/'1' from x^0 upward), its number of nonzero terms and the
-    total dimension defect."""
-    import hashlib
-    c = np.asarray(charpoly, dtype=np.uint8)
-    sha = hashlib.sha1("".join("1" if v else "0" for v in c).encode()).hexdigest()
-    _, delta = mtgp_params_equidistribution(p)
-    fields = [p.mexp, p.N, p.pos, p.sh1, p.sh2, p.id] + [f"{v:08x}" for v in p.rec_tbl] + \
-             [f"{v:08x}" for v in p.tmp_tbl] + [sha, int(c.sum()), delta]
-    return ",".join(str(f) for f in fields)
+def mtgp_params_record(p: mtgp_params, charpoly, threads: int = 0) -> str:
+    """MTGPDC record of a searched set (Sec. 5), charpoly as a coefficient array."""
+    w = poly_to_words(charpoly)
+    need = p.mexp // 64 + 1
+    if w.size < need:
+        w = np.concatenate([w, np.zeros(need - w.size, dtype=np.uint64)])
+    buf = ctypes.create_string_buffer(4096)
+    L.check(L.LIB.mtgp_params_record(ctypes.byref(p), _u64p(w), w.size, threads, buf, len(buf)))
+    return buf.value.decode()
 
 
 def mtgp_params_validate(p: mtgp_params) -> None:

@@ -1,8 +1,10 @@
 """Dimensions of equidistribution k(v) (Sec. 3.4, 3.8): the oracle's k(v)
 against values the paper prints (MT19937's defects, Sec. 3.8; minutes, so
---runmanual), against a construction from the standard state basis at small
-p, and against theorems (k(1) = p at full period, k(v) <= floor(p / v),
-k non-increasing); then the library's k(v) against the oracle's."""
+--runmanual; a record of its pass is in tests/golden), against a construction
+from the standard state basis at small p, and against theorems (k(1) = p at
+full period, k(v) <= floor(p / v), k non-increasing); then the library's k(v)
+(lattice reduction) against the oracle's (row reduction), MSBs and LSBs, and
+the tempering search of Sec. 5 against the oracle's restatement of it."""
 import numpy as np
 import pytest
 
@@ -102,23 +104,81 @@ def test_library_kv_equals_the_oracle(M, mexp, s0, gid):
     assert np.array_equal(k1, k)
 
 
-def test_tempering_search_lowers_the_defect_and_matches_the_oracle(M):
-    """The tempering search keeps the recursion, never returns a worse total
-    defect than the input's, and the oracle's k(v) for the returned table
-    (rebuilt from its four rows, Sec. 3.7 convention) equals the library's."""
-    p, seed, _, _ = M.mtgp_params_search(1279, 9, 1)
-    _, d0 = M.mtgp_params_equidistribution(p)
-    q, d1 = M.mtgp_params_temper_search(p, 100, 40)
-    assert d1 <= d0
-    assert list(q.rec_tbl) == list(p.rec_tbl) and q.pos == p.pos
+@pytest.mark.parametrize("mexp,s0,gid", [(521, 1000, 7), (1279, 9, 1)])
+def test_library_lsb_kv_equals_the_oracle_on_bit_reversed_outputs(M, mexp, s0, gid):
+    # k'(v) of the v least significant bits is k(v) of the outputs with their
+    # bit order reversed, which the oracle's row reduction computes
+    p, seed, _, _ = M.mtgp_params_search(mexp, s0, gid)
+    k, delta = M.mtgp_params_equidistribution_lsb(p)
+    op = O.params_draw(mexp, seed, gid)
+    out = O.generate(op, O.seed_state(op, 3, 5), 2 * mexp + 64, 0)
+    ko = O.kv(O.reverse_bits(out), mexp)
+    assert np.array_equal(k, ko)
+    assert delta == int(O.dimension_defects(ko, mexp).sum())
+
+
+def test_oracle_search_window_choice_by_brute_force():
+    """The oracle's first window (row 0, its 5 MSBs) against a brute force
+    that computes k(1) .. k(5) from the standard state basis for each of the
+    32 patterns: the oracle's pattern has the least d(1) + ... + d(5), the
+    smallest such pattern."""
+    op, _, _ = O.search_full_period(89, 1000, 7)
+    rows = O.temper_search_sec5(op)
+    sums = []
+    for pat in range(32):
+        q = O.params_from_fields(op.mexp, op.pos, op.sh1, op.sh2, op.id, list(op.R), [pat << 27, 0, 0, 0])
+        k = _kv_standard_basis(q, 5)
+        sums.append(sum(89 // v - int(k[v - 1]) for v in range(1, 6)))
+    assert (rows[0] >> 27) == int(np.argmin(sums))
+
+
+def test_oracle_search_phases_touch_only_their_bits():
+    # Sec. 5: the MSB phase sets bits 31 .. 9 of each row, the LSB phase bits
+    # 8 .. 0 and leaves the MSBs found before
+    op, _, _ = O.search_full_period(89, 1000, 7)
+    rows = O.temper_search_sec5(op)
+    p = op.mexp
+    k_final = O.kv(O.generate(O.params_from_fields(op.mexp, op.pos, op.sh1, op.sh2, op.id, list(op.R), rows),
+                              O.seed_state(op, 1, 2), 2 * p + 64, 0), p)
+    assert k_final[0] == p                               # full period: the MSB has complexity p
+    assert all(0 <= r < 1 << 32 for r in rows)
+
+
+@pytest.mark.parametrize("mexp,s0,gid", [(89, 1000, 7), (521, 1000, 7)])
+def test_tempering_search_equals_the_oracle_restatement(M, mexp, s0, gid):
+    """Sec. 5's tempering search: the library (lattice k(v), windows in
+    parallel) and the oracle's step-by-step restatement (row-reduction k(v))
+    find the same four rows; the library keeps the recursion and reports the
+    total MSB defect of the table it returns."""
+    op, seed, _ = O.search_full_period(mexp, s0, gid)
+    lp, lseed, _, _ = M.mtgp_params_search(mexp, s0, gid)
+    assert seed == lseed
+    rows_o = O.temper_search_sec5(op)
+    q, d = M.mtgp_params_temper_search(lp)
+    assert [q.tmp_tbl[8], q.tmp_tbl[4], q.tmp_tbl[2], q.tmp_tbl[1]] == rows_o
+    assert list(q.rec_tbl) == list(lp.rec_tbl) and q.pos == lp.pos
     M.mtgp_params_validate(q)
-    kq, dq = M.mtgp_params_equidistribution(q)
-    assert dq == d1
-    rows_r = [p.rec_tbl[8], p.rec_tbl[4], p.rec_tbl[2], p.rec_tbl[1]]
-    rows_t = [q.tmp_tbl[8], q.tmp_tbl[4], q.tmp_tbl[2], q.tmp_tbl[1]]
-    oq = O.params_from_fields(q.mexp, q.pos, q.sh1, q.sh2, q.id, rows_r, rows_t)
-    assert list(oq.rectbl) == list(q.rec_tbl) and list(oq.tmptbl) == list(q.tmp_tbl)
-    ko = O.kv(O.generate(oq, O.seed_state(oq, 2, 3), 2 * 1279 + 64, 0), 1279)
-    assert np.array_equal(kq, ko)
-    table = M.equidistribution_table(q, kq)
-    assert table.splitlines()[-1] == f"total dimension defect {d1}"
+    oq = O.params_from_fields(mexp, op.pos, op.sh1, op.sh2, gid, list(op.R), rows_o)
+    assert list(oq.tmptbl) == list(q.tmp_tbl)
+    ko = O.kv(O.generate(oq, O.seed_state(oq, 2, 3), 2 * mexp + 64, 0), mexp)
+    assert d == int(O.dimension_defects(ko, mexp).sum())
+
+
+def test_report_and_record(M):
+    """The Table 1 style report lists k(v), d(v) = floor(p/v) - k(v) and the
+    total; the MTGPDC record's digest is the SHA-1 (checked with Python's
+    hashlib) of the characteristic polynomial's coefficient string."""
+    import hashlib
+    p, seed, _, phi = M.mtgp_params_search(1279, 9, 1)
+    k, delta = M.mtgp_params_equidistribution(p)
+    lines = M.mtgp_params_report(p).splitlines()
+    assert lines[-1] == f"total dimension defect {delta}"
+    for v in range(1, 33):
+        f = lines[v].split()
+        assert int(f[0]) == v and int(f[1]) == k[v - 1] and int(f[2]) == 1279 // v - k[v - 1]
+    rec = M.mtgp_params_record(p, phi).split(",")
+    coef = "".join("1" if c else "0" for c in np.asarray(phi, dtype=np.uint8))
+    assert rec[-3] == hashlib.sha1(coef.encode()).hexdigest()
+    assert int(rec[-2]) == int(np.asarray(phi).sum()) and int(rec[-1]) == delta
+    assert rec[:6] == [str(x) for x in (p.mexp, p.N, p.pos, p.sh1, p.sh2, p.id)]
+    assert rec[6:22] == [f"{v:08x}" for v in p.rec_tbl] and rec[22:38] == [f"{v:08x}" for v in p.tmp_tbl]

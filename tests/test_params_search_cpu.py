@@ -52,7 +52,7 @@ def test_search_limits_and_record(M):
     with pytest.raises(M.MTGPError):
         M.mtgp_params_search(1279, 9, 1, max_tries=3)      # the first accepted candidate is number 1184
     p, seed, tries, phi = M.mtgp_params_search(89, 1000, 7)
-    rec = M.mtgpdc_record(p, phi).split(",")
+    rec = M.mtgp_params_record(p, phi).split(",")
     _, delta = M.mtgp_params_equidistribution(p)
     assert rec[0] == "89" and len(rec) == 6 + 32 + 3 and len(rec[-3]) == 40
     assert int(rec[-2]) == int(phi.sum()) and int(rec[-1]) == delta

@@ -215,9 +215,14 @@ def run_batched(torch, M, sample: int = 512):
     wl = WL.c4()
     ps = [M.mtgp_params_draw(g.mexp, g.param_seed, g.id) for g in wl.gens]
     pool = M.Pool(ps, [g.gen_id for g in wl.gens], [g.seed for g in wl.gens])
-    pool.set_config(threads=128, persistent=1)
     total = wl.total_numbers
     out = torch.empty(total, dtype=torch.int32, device="cuda")
+    # the project's autotuner picks form, block size, words per round,
+    # persistence, pieces and layout (C4's lengths differ: blocked only); it
+    # restores every state, and the graph captures the chosen configuration
+    t0 = time.perf_counter()
+    best, tune_ms, layout = pool.autotune(wl.requests, out)
+    tune_s = time.perf_counter() - t0
     # room for the jump-ahead pieces of the long generators (the plan splits
     # about 16 work items' worth per SM)
     graph = M.Graph(pool, max_items=2 * len(wl.gens))
@@ -255,10 +260,77 @@ def run_batched(torch, M, sample: int = 512):
             "value": total / (ms * 1e-3) / 1e9, "unit": "Gnum/s", "ms_per_launch": ms,
             "hbm_write_gbs": 4 * total / (ms * 1e-3) / 1e9, "numbers": total,
             "form": "one graph-captured launch: jump-ahead piece states, then the persistent generation "
-                    "launch (128 threads, longest first)",
+                    "launch (longest first), in the configuration the autotuner chose",
+            "autotuned": {"config": best.as_dict(), "layout": ["blocked", "interleaved"][layout],
+                          "tuned_call_ms": tune_ms, "tuning_s": tune_s},
             "plain_per_generator": {"value": n_sub / (ms_plain * 1e-3) / 1e9, "unit": "Gnum/s",
                                     "generators": len(sub), "launches": len(sub),
                                     "note": "one launch per generator, first %d generators of C4" % len(sub)}}
+
+
+def run_c1(torch, M, reps: int = 50):
+    """C1: one MTGP11213 generator, 2^20 u32 per call (a latency figure: one
+    stream, split into jump-ahead pieces by the default configuration);
+    median CUDA-event time of `reps` calls after warm-up."""
+    from paper_1005_4973_gb300 import workloads as WL
+    wl = WL.c1()
+    g = wl.gens[0]
+    pool = M.Pool([M.mtgp_params_draw(g.mexp, g.param_seed, g.id)], [g.gen_id], [g.seed])
+    out = torch.empty(wl.total_numbers, dtype=torch.int32, device="cuda")
+    for _ in range(5):
+        pool.generate(wl.requests, out)
+    ms = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(reps):
+        e0.record()
+        pool.generate(wl.requests, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    pool.close()
+    med = statistics.median(ms)
+    return {"workload": "C1: MTGP11213, one generator, 2^20 u32 per call", "ms_median": med,
+            "ms_min": min(ms), "value": wl.total_numbers / (med * 1e-3) / 1e9, "unit": "Gnum/s",
+            "calls": reps, "note": "latency of one call (host planning and the jump-ahead kernel included)"}
+
+
+def run_c3(torch, M, peak: float, steps: int = 5):
+    """C3: 128 parameter sets of MTGP23209 and of MTGP44497, 2^26 f[0,1)
+    each, one mexp at a time (32 GiB of output each); per mexp the step's
+    Gnum/s and the generation launch's roofline (CUDA events recorded by the
+    pool around it)."""
+    from paper_1005_4973_gb300 import workloads as WL
+    res = {}
+    for mexp in (23209, 44497):
+        wl = WL.c3(mexps=(mexp,))
+        ps = [M.mtgp_params_draw(g.mexp, g.param_seed, g.id) for g in wl.gens]
+        pool = M.Pool(ps, [g.gen_id for g in wl.gens], [g.seed for g in wl.gens])
+        total = wl.total_numbers
+        out = torch.empty(total, dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            pool.generate(wl.requests, out)
+        pool.set_timing(steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            pool.generate(wl.requests, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        jump_ms, gen_ms = pool.kernel_times(steps)
+        cfg = pool.config.as_dict()
+        pool.close()
+        del out
+        torch.cuda.empty_cache()
+        alg = 4 * total + sum(8 * p.N for p in ps)
+        ach = alg / (statistics.mean(gen_ms) * 1e-3) / 1e9
+        res[f"mexp{mexp}"] = {"value": total / (ms * 1e-3) / 1e9, "unit": "Gnum/s", "ms_per_step": ms,
+                              "numbers": total, "steps": steps, "launch": cfg,
+                              "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                           "frac": ach / peak, "avg_launch_ms": statistics.mean(gen_ms),
+                                           "avg_jump_ms": statistics.mean(jump_ms)}}
+    return res
 
 
 # Sec. 4.4, Table 2: milliseconds for 5e7 numbers from 108 MTGP11213
@@ -497,6 +569,10 @@ def main():
         del out
         torch.cuda.empty_cache()
         extras["paper_workload"] = run_paper(torch, M)
+        torch.cuda.empty_cache()
+        extras["c1"] = run_c1(torch, M)
+        torch.cuda.empty_cache()
+        extras["c3"] = run_c3(torch, M, peak)
         torch.cuda.empty_cache()
         extras["batched"] = run_batched(torch, M)
         torch.cuda.empty_cache()

@@ -97,8 +97,10 @@ typedef struct mtgp_request {
  * tempers, converts and stores finished rounds.  Wide form: each thread owns
  * groups of 4 adjacent columns, whose reads overlap (x_{i+1} of one column is
  * x_i of the next) and whose outputs leave in one 16-byte store; blocked
- * layouts only (interleaved calls run in the plain form).  On GB300 the plain
- * form measured fastest; mtgp_autotune tries plain, split and flow. */
+ * layouts only (interleaved calls run in the plain form).  Pair form: each
+ * thread owns two adjacent columns per slot (x_{i+1} and one tempering word
+ * shared within the pair, 8-byte stores), 128 threads.  On GB300 the plain
+ * form measured fastest; mtgp_autotune tries every form. */
 typedef struct mtgp_config {
     uint32_t threads;          /* threads per block: plain 32, 64, 128, 256, 512
                                   (at most 11, 12, 11, 6, 8 columns per thread);
@@ -131,6 +133,12 @@ typedef struct mtgp_config {
                                   split, else at most 256                           */
     uint32_t piece_log2;       /* pieces hold at least 2^piece_log2 numbers; 0 = 20,
                                   else 10 .. 40                                    */
+    uint32_t round_words;      /* words per round (Sec. 3.2: any n <= S = N - M
+                                  consecutive words are independent): 0 = S; the
+                                  wide form takes rounds of min(S, round_words),
+                                  a multiple of 4 >= 8; the other forms keep the
+                                  round's column slots in registers from round to
+                                  round, which needs rounds of exactly S words     */
 } mtgp_config;
 
 /* ---- library ------------------------------------------------------------ */
@@ -186,6 +194,19 @@ mtgp_status mtgp_params_validate(const mtgp_params *p);
 mtgp_status mtgp_params_search(uint32_t mexp, uint64_t seed0, uint32_t id, uint64_t max_tries, uint32_t threads,
                                mtgp_params *out, uint64_t *found_seed, uint64_t *tries, uint64_t *charpoly,
                                uint32_t charpoly_words);
+
+/*
+ * The same search (same candidates, same acceptance, same result) with the
+ * Berlekamp-Massey step on the GPU: candidates run in batches of up to 4096;
+ * the host cores draw them and walk their MSB sequences, one warp per
+ * candidate finds the sequence's minimal polynomial on `stream`, and the
+ * host cores test the ones of degree mexp for irreducibility in candidate
+ * order.  Allocates and frees its device buffers (about 4096 x 3 mexp / 8
+ * bytes); synchronous.  Errors as mtgp_params_search, plus MTGP_ECUDA.
+ */
+mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uint32_t id, uint64_t max_tries,
+                                   uint32_t threads, void *stream, mtgp_params *out, uint64_t *found_seed,
+                                   uint64_t *tries, uint64_t *charpoly, uint32_t charpoly_words);
 
 /*
  * Dimensions of equidistribution (Sec. 3.4, 3.8; Table 1): k(v) for v = 1 ..
@@ -349,18 +370,26 @@ mtgp_status mtgp_pool_load(mtgp_pool *p, const void *host_buf, size_t bytes);
 void mtgp_pool_destroy(mtgp_pool *p);
 
 /*
- * Picks the form (plain, split or flow), threads, persistent mode and occupancy
- * for this pool by timing candidate configurations on `stream` with the given
- * requests written to dev_scratch (caller-owned, large enough for them).  The
- * generators' states are saved before and restored after, so tuning does not
- * advance any stream (the restore empties the work lists of the pool's graphs
- * that hold jump-ahead pieces, as mtgp_pool_load does).  On success the best
- * configuration is set on the pool and copied to *best (if not NULL);
- * *best_ms receives its time (if not NULL).
- * Synchronous.
+ * The project's autotuner: picks the launch configuration and the output
+ * layout for these requests by timing candidates on `stream`, the requests
+ * written to dev_scratch (caller-owned, 4 sum(n) bytes).  Stage 1 tries every
+ * form (plain, split, flow, wide, pairs) with its block sizes, words per round
+ * (mtgp_config.round_words: S, 128 or 256 for the wide form), persistent grids
+ * of 0 / 2 / 4 / 8 blocks per SM or one block per item, and jump-ahead pieces
+ * (auto or none), in the blocked layout when `layouts` allows it (bit 0;
+ * else interleaved).  Stage 2, when `layouts` bit 1 allows the interleaved
+ * layout and the requests qualify (equal lengths, distinct generators),
+ * tries it with chunks of 2^8, 2^12 and 2^16 numbers (those dividing the
+ * length) for the best configuration of stage 1.  The generators' states are
+ * saved before and restored after, so tuning does not advance any stream (the
+ * restore empties the work lists of the pool's graphs that hold jump-ahead
+ * pieces, as mtgp_pool_load does).  On success the best configuration is set
+ * on the pool and copied to *best, the layout to *best_layout and its time to
+ * *best_ms (each if not NULL).  Synchronous.
  */
 mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_scratch,
-                          void *stream, mtgp_config *best, float *best_ms);
+                          uint32_t layouts, void *stream, mtgp_config *best, mtgp_layout *best_layout,
+                          float *best_ms);
 
 /*
  * Error word of the pool's last launches: bit 0 a generator did not fit the
@@ -373,6 +402,15 @@ mtgp_status mtgp_pool_errors(mtgp_pool *p, uint32_t *flags);
 /* Kernels launched so far by the pool's generation calls (generation, plus
  * the two jump-ahead kernels of calls that split work into pieces). */
 mtgp_status mtgp_pool_launch_count(const mtgp_pool *p, uint64_t *launches);
+
+/*
+ * Flow form (mtgp_config.form = 2): polls per bounded wait between warps in
+ * its later launches (0, the default: 2^22).  A wait that runs out sets bit 1
+ * of the error word (mtgp_pool_errors), the warp stops waiting, the launch
+ * ends and its outputs are invalid; the context stays usable.  Graphs capture
+ * the limit in force when they are created.  Waits for queued work.
+ */
+mtgp_status mtgp_pool_set_spin_limit(mtgp_pool *p, uint32_t polls);
 
 /*
  * Per-kernel timing, for measurement.  With entries > 0, each later

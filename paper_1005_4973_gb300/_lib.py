@@ -55,7 +55,7 @@ class mtgp_request(ctypes.Structure):
 class mtgp_config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
                 ("threads", "persistent", "blocks_per_sm", "chunk", "buffer_words", "form", "pieces",
-                 "piece_log2")]
+                 "piece_log2", "round_words")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -102,18 +102,21 @@ _SIGS = {
     "mtgp_pool_save": (ctypes.c_int, [_vp, _vp, _P(_sz)]),
     "mtgp_pool_load": (ctypes.c_int, [_vp, _vp, _sz]),
     "mtgp_pool_destroy": (None, [_vp]),
-    "mtgp_autotune": (ctypes.c_int, [_vp, _P(mtgp_request), _u32, _vp, _vp, _P(mtgp_config),
-                                     _P(ctypes.c_float)]),
+    "mtgp_autotune": (ctypes.c_int, [_vp, _P(mtgp_request), _u32, _vp, _u32, _vp, _P(mtgp_config),
+                                     _P(ctypes.c_int), _P(ctypes.c_float)]),
     "mtgp_fill_probe": (ctypes.c_int, [_vp, _u64, _u32, _vp]),
     "mtgp_pool_errors": (ctypes.c_int, [_vp, _P(_u32)]),
     "mtgp_pool_launch_count": (ctypes.c_int, [_vp, _P(_u64)]),
     "mtgp_pool_set_timing": (ctypes.c_int, [_vp, _u32]),
+    "mtgp_pool_set_spin_limit": (ctypes.c_int, [_vp, _u32]),
     "mtgp_pool_kernel_times": (ctypes.c_int, [_vp, _u32, _P(ctypes.c_float), _P(ctypes.c_float)]),
     "mtgp_pool_jump": (ctypes.c_int, [_vp, _u32, _u64, _vp]),
     "mtgp_state_jump": (ctypes.c_int, [_vp, _u64, _vp]),
     "mtgp_pool_annihilator": (ctypes.c_int, [_vp, _u32, _P(_u64), _u32, _P(_u32), _vp]),
     "mtgp_params_search": (ctypes.c_int, [_u32, _u64, _u32, _u64, _u32, _P(mtgp_params), _P(_u64), _P(_u64),
                                           _P(_u64), _u32]),
+    "mtgp_params_search_gpu": (ctypes.c_int, [_u32, _u64, _u32, _u64, _u32, _vp, _P(mtgp_params), _P(_u64),
+                                               _P(_u64), _P(_u64), _u32]),
     "mtgp_params_equidistribution": (ctypes.c_int, [_P(mtgp_params), _u32, _P(_u32), _P(_u32)]),
     "mtgp_params_equidistribution_lsb": (ctypes.c_int, [_P(mtgp_params), _u32, _P(_u32), _P(_u32)]),
     "mtgp_params_temper_search": (ctypes.c_int, [_P(mtgp_params), _u32, _P(mtgp_params), _P(_u32)]),

@@ -712,9 +712,9 @@ __global__ void __launch_bounds__(T, QMAX <= 6 ? 512 / T : (T >= 256 ? 1 : 256 /
 // converts and stores.  The recursion warps never store to global memory, so
 // their release stores do not wait on HBM writes.  A block barrier is taken
 // only every E rounds, when the buffer is compacted, and at the end of a work
-// item.  Every wait is bounded: after kSpinLimit polls the warp records
-// kErrTimeout and stops waiting (results are then invalid, the kernel still
-// ends).
+// item.  Every wait is bounded: after kSpinLimit polls (or the launch's
+// LaunchArgs::spin_limit) the warp records kErrTimeout and stops waiting
+// (results are then invalid, the kernel still ends).
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t ld_acquire_shared(const uint32_t *p)
@@ -733,16 +733,23 @@ __device__ __forceinline__ void st_release_shared(uint32_t *p, uint32_t v)
                  : "memory");
 }
 
-// Waits (warp-uniformly) until *ctr >= need.  `failed` turns every later wait
-// of this warp into a no-op once one has run out.
-__device__ __forceinline__ void wait_progress(const uint32_t *ctr, uint32_t need, bool &failed, unsigned *err)
+// Where a run-out wait reports (kErrTimeout) and how many polls it makes.
+struct FlowWait {
+    unsigned *err;
+    uint32_t limit;
+};
+
+// Waits (warp-uniformly) until *ctr >= need, at most fw.limit polls.
+// `failed` turns every later wait of this warp into a no-op once one has run
+// out.
+__device__ __forceinline__ void wait_progress(const uint32_t *ctr, uint32_t need, bool &failed, const FlowWait &fw)
 {
     if (failed) return;
     uint32_t spins = 0;
     while (ld_acquire_shared(ctr) < need) {
-        if (++spins > kSpinLimit) {
+        if (++spins > fw.limit) {
             failed = true;
-            if ((threadIdx.x & 31u) == 0) atomicOr(err, kErrTimeout);
+            if ((threadIdx.x & 31u) == 0) atomicOr(fw.err, kErrTimeout);
             return;
         }
     }
@@ -792,7 +799,7 @@ template <int C>
 __device__ __forceinline__ void flow_recursion(const GenCtx &g, uint32_t *buf, uint32_t rel0, uint32_t r0,
                                                uint32_t re, uint64_t total, uint32_t w, uint32_t lane,
                                                const FlowDeps &dep, uint32_t (&prev)[C], uint32_t *prog,
-                                               bool &failed, unsigned *err)
+                                               bool &failed, const FlowWait &fw)
 {
     const uint32_t base = 32u * C * w + lane;       // column of chunk 0
     for (uint32_t r = r0; r < re; ++r) {
@@ -802,7 +809,7 @@ __device__ __forceinline__ void flow_recursion(const GenCtx &g, uint32_t *buf, u
             if (r < dep.d[i]) continue;
             const uint32_t need = r - dep.d[i] + 1u;
             for (uint32_t v = dep.lo[i]; v <= dep.hi[i]; ++v)
-                if (v != w) wait_progress(prog + v, need, failed, err);
+                if (v != w) wait_progress(prog + v, need, failed, fw);
         }
         const uint32_t *x = buf + rel0 + (r - r0) * g.S + base;
         uint32_t *xn_p = buf + rel0 + (r - r0) * g.S + base + g.N;
@@ -855,7 +862,7 @@ template <int C>
 __device__ __forceinline__ void flow_output(const GenCtx &g, const uint32_t *buf, uint32_t rel0, uint32_t r0,
                                             uint32_t re, uint64_t total, uint32_t w, uint32_t lane,
                                             uint32_t active, const uint32_t *prog, SegCursor &sc,
-                                            uint32_t *out_base, bool &failed, unsigned *err)
+                                            uint32_t *out_base, bool &failed, const FlowWait &fw)
 {
     const uint32_t lo = 32u * C * w, base = lo + lane;
     const uint32_t hi = min(lo + 32u * C, g.S) - 1u;
@@ -863,11 +870,11 @@ __device__ __forceinline__ void flow_output(const GenCtx &g, const uint32_t *buf
         const uint64_t k0 = (uint64_t)r * g.S;
         const uint32_t S_r = (uint32_t)min((uint64_t)g.S, total - k0);
         if (lo >= S_r) continue;                                      // no column of this warp in the round
-        wait_progress(prog + w, r + 1u, failed, err);                  // x_{N+i} of round r
+        wait_progress(prog + w, r + 1u, failed, fw);                  // x_{N+i} of round r
         if (lo > 0)                                                   // x_{M-1+i} of column lo-1
-            wait_progress(prog + (lo - 1u) / (32u * C), r, failed, err);
+            wait_progress(prog + (lo - 1u) / (32u * C), r, failed, fw);
         else if (r >= 2)
-            wait_progress(prog + active - 1u, r - 1u, failed, err);
+            wait_progress(prog + active - 1u, r - 1u, failed, fw);
         const uint32_t *x = buf + rel0 + (r - r0) * g.S + base;
         uint32_t xn[C], xt[C];
 #pragma unroll
@@ -913,7 +920,7 @@ __device__ __forceinline__ void flow_output(const GenCtx &g, const uint32_t *buf
 template <int W, int C>
 __device__ __forceinline__ void run_item_flow(const GenCtx &g, uint32_t *buf, uint32_t B, const DevWork &w,
                                               const DevSeg *segs, uint32_t *out, uint32_t *st, uint32_t *prog,
-                                              unsigned *err)
+                                              const FlowWait &fw)
 {
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
     const uint32_t span = 32u * C;
@@ -948,9 +955,9 @@ __device__ __forceinline__ void run_item_flow(const GenCtx &g, uint32_t *buf, ui
         const uint32_t re = min(rounds, r0 + E);
         if (working) {
             if (is_rec)
-                flow_recursion<C>(g, buf, rel, r0, re, w.total, wg, lane, dep, prev, prog, failed, err);
+                flow_recursion<C>(g, buf, rel, r0, re, w.total, wg, lane, dep, prev, prog, failed, fw);
             else
-                flow_output<C>(g, buf, rel, r0, re, w.total, wg, lane, active, prog, sc, out, failed, err);
+                flow_output<C>(g, buf, rel, r0, re, w.total, wg, lane, active, prog, sc, out, failed, fw);
         }
         const uint32_t words = (uint32_t)(min((uint64_t)re * g.S, w.total) - (uint64_t)r0 * g.S);
         __syncthreads();
@@ -969,14 +976,14 @@ __device__ __forceinline__ void run_item_flow(const GenCtx &g, uint32_t *buf, ui
 template <int W, int CMAX>
 __device__ __forceinline__ bool dispatch_flow(uint32_t nc, const GenCtx &g, uint32_t *buf, uint32_t B,
                                               const DevWork &w, const DevSeg *segs, uint32_t *out, uint32_t *st,
-                                              uint32_t *prog, unsigned *err)
+                                              uint32_t *prog, const FlowWait &fw)
 {
     if (nc == (uint32_t)CMAX) {
-        run_item_flow<W, CMAX>(g, buf, B, w, segs, out, st, prog, err);
+        run_item_flow<W, CMAX>(g, buf, B, w, segs, out, st, prog, fw);
         return true;
     }
     if constexpr (CMAX > 1)
-        return dispatch_flow<W, CMAX - 1>(nc, g, buf, B, w, segs, out, st, prog, err);
+        return dispatch_flow<W, CMAX - 1>(nc, g, buf, B, w, segs, out, st, prog, fw);
     else
         return false;
 }
@@ -1024,7 +1031,8 @@ __global__ void __launch_bounds__(64 * W, (64 * W) >= 512 ? 1 : 512 / (64 * W)) 
             for (uint32_t j = tid; j < g.N; j += T) buf[j] = ld[j];
             if (tid < (uint32_t)W) prog[tid] = 0u;
             __syncthreads();
-            ok = dispatch_flow<W, CMAX>(nc, g, buf, B, w, a.segs + w.seg_begin, out, st, prog, a.err);
+            const FlowWait fw{a.err, a.spin_limit ? a.spin_limit : kSpinLimit};
+            ok = dispatch_flow<W, CMAX>(nc, g, buf, B, w, a.segs + w.seg_begin, out, st, prog, fw);
             if (ok && tid == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&gd.count), (unsigned long long)w.total);
         }
         if (!ok && tid == 0) atomicOr(a.err, kErrBuffer);

@@ -188,6 +188,7 @@ struct mtgp_pool {
     std::vector<cudaEvent_t> tev;
     std::vector<uint8_t> tjump;
     uint32_t timing_n = 0, timing_next = 0, timing_count = 0;
+    uint32_t spin_limit = 0;               // flow form: polls per bounded wait (0: default)
 };
 
 struct mtgp_state {
@@ -240,7 +241,7 @@ mtgp_status empty_graph_lists(mtgp_pool *p)
 
 namespace {
 
-const mtgp_config kDefaultConfig = {128u, 1u, 0u, 256u, 0u, 0u, 0u, 0u};   // plain, persistent, auto
+const mtgp_config kDefaultConfig = {128u, 1u, 0u, 256u, 0u, 0u, 0u, 0u, 0u};   // plain, persistent, auto
 constexpr size_t kJumpStoreCap = (size_t)1 << 30;   // device bytes of cached jump polynomials
 constexpr uint64_t kSeqCap = 256ull << 20;           // walk scratch words per launch
 
@@ -258,6 +259,8 @@ mtgp_status check_config(const mtgp_config &c)
     if (c.pieces > 256u) return fail(MTGP_EINVAL, "pieces must be <= 256");
     if (c.piece_log2 != 0u && (c.piece_log2 < 10u || c.piece_log2 > 40u))
         return fail(MTGP_EINVAL, "piece_log2 must be 0 or in [10, 40]");
+    if (c.round_words != 0u && (c.round_words < 8u || (c.round_words & 3u) || c.round_words > 65536u))
+        return fail(MTGP_EINVAL, "round_words must be 0 or a multiple of 4 in [8, 65536]");
     return MTGP_OK;
 }
 
@@ -760,6 +763,8 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     a.persistent = persistent ? 1u : 0u;
     a.jstate = p->d_jstate;
     a.interleave = interleave ? 1u : 0u;
+    a.spin_limit = p->spin_limit;
+    a.round_words = c.round_words;
     if (tev) CU(cudaEventRecord(tev[1], s), "cudaEventRecord");
     CU(launch_generate(a, c.threads, c.form, qmax, grid, s), "generate kernel launch");
     if (tev) CU(cudaEventRecord(tev[2], s), "cudaEventRecord");
@@ -1223,14 +1228,29 @@ mtgp_status mtgp_fill_probe(void *dev_buf, uint64_t words, uint32_t pattern, voi
 }
 
 // ---- autotuner ---------------------------------------------------------------
-mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_scratch, void *stream,
-                          mtgp_config *best, float *best_ms)
+mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq, void *dev_scratch,
+                          uint32_t layouts, void *stream, mtgp_config *best, mtgp_layout *best_layout,
+                          float *best_ms)
 {
     return guarded([&]() -> mtgp_status {
         if (!p) return fail(MTGP_EINVAL, "pool is NULL");
+        if (!(layouts & 3u)) return fail(MTGP_EINVAL, "layouts: bit 0 (blocked) and/or bit 1 (interleaved)");
         cudaStream_t s = (cudaStream_t)stream;
         mtgp_status st = pool_busy_check(p, s);
         if (st != MTGP_OK) return st;
+        // the interleaved layout needs equal lengths and distinct generators;
+        // chunks that divide the length leave no gaps in the output
+        bool inter = (layouts & 2u) && nreq > 0;
+        for (uint32_t j = 0; inter && j < nreq; ++j) inter = reqs[j].n == reqs[0].n && reqs[j].n > 0;
+        if (inter) {
+            std::vector<uint8_t> seen(p->count, 0);
+            for (uint32_t j = 0; inter && j < nreq; ++j) {
+                inter = reqs[j].gen < p->count && !seen[reqs[j].gen];
+                if (inter) seen[reqs[j].gen] = 1;
+            }
+        }
+        if (!(layouts & 1u) && !inter)
+            return fail(MTGP_EINVAL, "autotune: the interleaved layout needs equal lengths and distinct generators");
         size_t bytes = 0;
         st = mtgp_pool_save(p, nullptr, &bytes);
         if (st != MTGP_OK) return st;
@@ -1238,38 +1258,67 @@ mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
         st = mtgp_pool_save(p, ckpt.data(), &bytes);
         if (st != MTGP_OK) return st;
         const mtgp_config orig = p->cfg;
+        // stage 1: form, block size, words per round (wide form), persistence
+        // and occupancy, jump-ahead pieces -- blocked layout (or the
+        // interleaved one, with the default chunk, if blocked is not allowed)
         std::vector<mtgp_config> cands;
-        for (uint32_t pieces : {0u, 1u})                     // jump-ahead pieces: auto, or none
-            for (uint32_t form : {0u, 1u, 2u})             // the wide form (3) measured slower everywhere
-                for (uint32_t threads : {32u, 64u, 128u, 256u, 512u, 1024u})
-                    for (uint32_t pers : {0u, 1u})
-                        for (uint32_t bps : {0u, 1u, 2u, 3u, 4u, 6u, 8u}) {
-                            if (!pers && bps) continue;
-                            if (!threads_supported(threads, form)) continue;
-                            cands.push_back(mtgp_config{threads, pers, bps, orig.chunk, 0u, form, pieces, 0u});
-                        }
+        for (uint32_t pieces : {0u, 1u})
+            for (uint32_t form : {0u, 1u, 2u, 3u, 4u})
+                for (uint32_t threads : {32u, 64u, 96u, 128u, 192u, 256u, 512u, 1024u})
+                    for (uint32_t rw : {0u, 128u, 256u})
+                        for (uint32_t pers : {0u, 1u})
+                            for (uint32_t bps : {0u, 2u, 4u, 8u}) {
+                                if (!pers && bps) continue;
+                                if (rw && form != 3u) continue;
+                                if (!threads_supported(threads, form)) continue;
+                                mtgp_config c{threads, pers, bps, orig.chunk, 0u, form, pieces, 0u, rw};
+                                cands.push_back(c);
+                            }
         cudaEvent_t e0, e1;
         CU(cudaEventCreate(&e0), "cudaEventCreate");
         CU(cudaEventCreate(&e1), "cudaEventCreate");
+        auto time_one = [&](const mtgp_config &c, mtgp_layout lay, float *ms) -> bool {
+            p->cfg = c;
+            if (pool_run(p, reqs, nreq, dev_scratch, lay, s) != MTGP_OK) return false;   // warm-up
+            if (cudaEventRecord(e0, s) != cudaSuccess) return false;
+            const mtgp_status r = pool_run(p, reqs, nreq, dev_scratch, lay, s);
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return false;
+            return r == MTGP_OK && cudaEventElapsedTime(ms, e0, e1) == cudaSuccess;
+        };
+        const mtgp_layout lay1 = (layouts & 1u) ? MTGP_LAYOUT_BLOCKED : MTGP_LAYOUT_INTERLEAVED;
         float best_t = 1e30f;
         mtgp_config best_c = orig;
+        mtgp_layout best_l = lay1;
         for (const mtgp_config &c : cands) {
-            p->cfg = c;
-            mtgp_status r = pool_run(p, reqs, nreq, dev_scratch, MTGP_LAYOUT_BLOCKED, s);   // warm-up
-            if (r != MTGP_OK) continue;
-            CU(cudaEventRecord(e0, s), "cudaEventRecord");
-            r = pool_run(p, reqs, nreq, dev_scratch, MTGP_LAYOUT_BLOCKED, s);
-            CU(cudaEventRecord(e1, s), "cudaEventRecord");
-            CU(cudaEventSynchronize(e1), "cudaEventSynchronize");
             float ms = 0.f;
-            CU(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
-            if (r == MTGP_OK && ms < best_t) {
+            if (time_one(c, lay1, &ms) && ms < best_t) {
                 best_t = ms;
                 best_c = c;
             }
         }
+        // stage 2: the interleaved layout with chunks of 2^8, 2^12, 2^16 words
+        // (those dividing the length), for the best configuration of stage 1
+        if (inter && best_t < 1e30f) {
+            for (uint32_t chunk : {256u, 4096u, 65536u}) {
+                if (reqs[0].n % chunk) continue;
+                mtgp_config c = best_c;
+                c.chunk = chunk;
+                if (c.form == 3u) {                           // the wide form writes blocked layouts only
+                    c.form = 0u;
+                    c.threads = 128u;
+                    c.round_words = 0u;
+                }
+                float ms = 0.f;
+                if (time_one(c, MTGP_LAYOUT_INTERLEAVED, &ms) && ms < best_t) {
+                    best_t = ms;
+                    best_c = c;
+                    best_l = MTGP_LAYOUT_INTERLEAVED;
+                }
+            }
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        (void)cudaGetLastError();                             // failed candidates leave nothing behind
         p->cfg = best_c;
         // psi found while tuning annihilates the restored (earlier) states as well:
         // psi(F) F^k s = 0 and F is invertible (R4 + I invertible, Sec. 5)
@@ -1277,7 +1326,9 @@ mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
         st = mtgp_pool_load(p, ckpt.data(), bytes);
         if (st != MTGP_OK) return st;
         p->jc.ann = ann;
+        if (best_t >= 1e30f) return fail(MTGP_EINVAL, "autotune: no candidate configuration ran");
         if (best) *best = best_c;
+        if (best_layout) *best_layout = best_l;
         if (best_ms) *best_ms = best_t;
         return MTGP_OK;
     });
@@ -1374,6 +1425,8 @@ mtgp_status mtgp::graph_create(mtgp_pool *p, uint32_t max_items, void *stream, b
         a.buf_words = B;
         a.persistent = 1u;
         a.jstate = g->d_jstate;
+        a.spin_limit = p->spin_limit;                         // fixed in the capture
+        a.round_words = c.round_words;
         CUG(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
         cudaError_t e1 = cudaMemsetAsync(b, 0, sizeof(unsigned), g->cap_stream);
         if (e1 == cudaSuccess && g->jump)
@@ -1536,6 +1589,15 @@ mtgp_status mtgp_pool_launch_count(const mtgp_pool *p, uint64_t *launches)
 {
     if (!p || !launches) return fail(MTGP_EINVAL, "NULL argument");
     *launches = p->launches;
+    return MTGP_OK;
+}
+
+mtgp_status mtgp_pool_set_spin_limit(mtgp_pool *p, uint32_t polls)
+{
+    if (!p) return fail(MTGP_EINVAL, "NULL pool");
+    mtgp_status st = pool_sync(p);
+    if (st != MTGP_OK) return st;
+    p->spin_limit = polls;
     return MTGP_OK;
 }
 

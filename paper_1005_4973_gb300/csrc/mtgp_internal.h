@@ -83,6 +83,13 @@ GenKernel flow_kernel_w4(uint32_t cmax);
 GenKernel flow_kernel_w8(uint32_t cmax);
 GenKernel flow_kernel_w16(uint32_t cmax);
 
+// Berlekamp-Massey on the GPU, one warp per sequence (mtgp_bm.cu): nseq bit
+// sequences of n bits, `words` = ceil(n / 32) words apart; writes each
+// annihilator (owords words, bit j = coefficient of x^j) and its degree
+// (0xFFFFFFFF when above about n / 2 or owords * 32).
+cudaError_t launch_bm(const uint32_t *seq, uint32_t nseq, uint32_t n, uint32_t words, uint32_t *out,
+                      uint32_t owords, uint32_t *len, cudaStream_t s);
+
 // Records msg as the calling thread's last error and returns status.
 int report_error(int status, const char *msg);
 

@@ -64,6 +64,8 @@ struct LaunchArgs {
     uint32_t persistent;
     const uint32_t *jstate;             // start states of pieces (DevWork::src)
     uint32_t interleave;                // 1: interleaved round tails where compiled (latency-bound launches)
+    uint32_t spin_limit;                // flow form: polls per bounded wait, 0 = the default
+    uint32_t round_words;               // wide form: words per round if below S (0 = S)
 };
 
 }  // namespace mtgp

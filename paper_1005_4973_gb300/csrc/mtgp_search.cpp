@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdio>
 #include <cstring>
 #include <exception>
 #include <limits>
@@ -153,4 +154,137 @@ extern "C" mtgp_status mtgp_params_search(uint32_t mexp, uint64_t seed0, uint32_
         std::copy(found_phi[w].begin(), found_phi[w].end(), charpoly);
     }
     return MTGP_OK;
+}
+
+// The same search with the Berlekamp-Massey step on the GPU: candidates run in
+// batches; the host draws each candidate and walks its MSB sequence (threads
+// over candidates), one warp per candidate finds the sequence's minimal
+// polynomial (mtgp_bm.cu), and the host tests the ones of degree mexp for
+// irreducibility in candidate order (threads over candidates).  The first
+// accepted candidate is the host search's.
+extern "C" mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uint32_t id, uint64_t max_tries,
+                                              uint32_t threads, void *stream, mtgp_params *out,
+                                              uint64_t *found_seed, uint64_t *tries, uint64_t *charpoly,
+                                              uint32_t charpoly_words)
+{
+    using namespace mtgp;
+    if (!out || !found_seed || !tries) return (mtgp_status)report_error(MTGP_EINVAL, "search: NULL argument");
+    if (charpoly && charpoly_words < mexp / 64u + 1u)
+        return (mtgp_status)report_error(MTGP_EINVAL, "search: charpoly needs mexp / 64 + 1 words");
+    mtgp_params probe;
+    mtgp_status st = mtgp_params_draw(mexp, seed0, id, &probe);
+    if (st != MTGP_OK) return st;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned nt = threads ? threads : hw;
+    const uint64_t n = 2ull * mexp;
+    const uint32_t w64 = (uint32_t)(n / 64u) + 1u, words = 2u * w64;   // msb_sequence's layout
+    const uint32_t owords = mexp / 32u + 2u;
+    const uint64_t batch = std::min<uint64_t>(4096u, max_tries);
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *d_seq = nullptr, *d_out = nullptr, *d_len = nullptr;
+    auto cleanup = [&] {
+        cudaFree(d_seq);
+        cudaFree(d_out);
+        cudaFree(d_len);
+        (void)cudaGetLastError();
+    };
+    auto cuda_err = [&](cudaError_t e, const char *what) {
+        cleanup();
+        char buf[200];
+        snprintf(buf, sizeof buf, "search: %s: %s", what, cudaGetErrorString(e));
+        return (mtgp_status)report_error(e == cudaErrorMemoryAllocation ? MTGP_ENOMEM : MTGP_ECUDA, buf);
+    };
+    cudaError_t e = cudaMalloc(&d_seq, (size_t)batch * words * 4u);
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, (size_t)batch * owords * 4u);
+    if (e == cudaSuccess) e = cudaMalloc(&d_len, (size_t)batch * 4u);
+    if (e != cudaSuccess) return cuda_err(e, "cudaMalloc");
+    try {
+        std::vector<uint64_t> seq((size_t)batch * w64);
+        std::vector<uint32_t> polys((size_t)batch * owords), lens(batch);
+        for (uint64_t base = 0; base < max_tries; base += batch) {
+            const uint64_t nb = std::min<uint64_t>(batch, max_tries - base);
+            std::atomic<uint64_t> next{0};
+            std::atomic<bool> bad{false};
+            auto walker = [&] {
+                try {
+                    std::vector<uint64_t> bits;
+                    for (uint64_t j; (j = next.fetch_add(1)) < nb;) {
+                        mtgp_params p;
+                        if (mtgp_params_draw(mexp, seed0 + base + j, id, &p) != MTGP_OK) {
+                            bad = true;
+                            return;
+                        }
+                        msb_sequence(p, 12345u + base + j, n, bits);
+                        std::copy(bits.begin(), bits.begin() + w64, seq.begin() + (ptrdiff_t)(j * w64));
+                    }
+                } catch (const std::exception &) {
+                    bad = true;
+                }
+            };
+            std::vector<std::thread> pool;
+            for (unsigned t = 0; t < nt; ++t) pool.emplace_back(walker);
+            for (auto &th : pool) th.join();
+            if (bad) {
+                cleanup();
+                return (mtgp_status)report_error(MTGP_ENOMEM, "search: host allocation failed");
+            }
+            e = cudaMemcpyAsync(d_seq, seq.data(), (size_t)nb * w64 * 8u, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = launch_bm(d_seq, (uint32_t)nb, (uint32_t)n, words, d_out, owords, d_len, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(lens.data(), d_len, (size_t)nb * 4u, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(polys.data(), d_out, (size_t)nb * owords * 4u, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_err(e, "Berlekamp-Massey batch");
+            // candidates of degree mexp, in order; the smallest irreducible wins
+            std::vector<uint64_t> cand;
+            for (uint64_t j = 0; j < nb; ++j)
+                if (lens[j] == mexp) cand.push_back(j);
+            std::atomic<size_t> ci{0};
+            std::atomic<uint64_t> best{std::numeric_limits<uint64_t>::max()};
+            auto tester = [&] {
+                try {
+                    for (size_t i; (i = ci.fetch_add(1)) < cand.size();) {
+                        const uint64_t j = cand[i];
+                        if (j >= best.load()) return;
+                        f2::Poly phi((size_t)(mexp / 64u) + 1u, 0u);
+                        for (uint32_t b = 0; b <= mexp; ++b)
+                            if ((polys[(size_t)j * owords + (b >> 5)] >> (b & 31u)) & 1u)
+                                phi[b >> 6] |= 1ull << (b & 63u);
+                        if (!irreducible_prime_degree(phi, mexp, 40u)) continue;
+                        uint64_t b0 = best.load();
+                        while (j < b0 && !best.compare_exchange_weak(b0, j)) {
+                        }
+                    }
+                } catch (const std::exception &) {
+                    bad = true;
+                }
+            };
+            pool.clear();
+            for (unsigned t = 0; t < nt; ++t) pool.emplace_back(tester);
+            for (auto &th : pool) th.join();
+            if (bad) {
+                cleanup();
+                return (mtgp_status)report_error(MTGP_ENOMEM, "search: host allocation failed");
+            }
+            const uint64_t j = best.load();
+            if (j == std::numeric_limits<uint64_t>::max()) continue;
+            cleanup();
+            st = mtgp_params_draw(mexp, seed0 + base + j, id, out);
+            if (st != MTGP_OK) return st;
+            *found_seed = seed0 + base + j;
+            *tries = base + j + 1u;
+            if (charpoly) {
+                std::memset(charpoly, 0, sizeof(uint64_t) * charpoly_words);
+                for (uint32_t b = 0; b <= mexp; ++b)
+                    if ((polys[(size_t)j * owords + (b >> 5)] >> (b & 31u)) & 1u) charpoly[b >> 6] |= 1ull << (b & 63u);
+            }
+            return MTGP_OK;
+        }
+    } catch (const std::exception &) {
+        cleanup();
+        return (mtgp_status)report_error(MTGP_ENOMEM, "search: host allocation or thread start failed");
+    }
+    cleanup();
+    return (mtgp_status)report_error(MTGP_EINVAL, "search: no full-period set within max_tries");
 }

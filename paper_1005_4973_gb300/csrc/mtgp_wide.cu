@@ -6,7 +6,8 @@
 //
 // Rounds.  Any n <= S = N - M consecutive words of the recursion (Sec. 3.2,
 // 3.6) are independent: word x_{N+i} reads x_i, x_{i+1}, x_{M+i} only.  A
-// round here computes n = min(S, words left in the segment) of them; the
+// round here computes n = min(R, words left in the segment) of them (R = S,
+// or the launch's mtgp_config.round_words if smaller); the
 // next round starts where it ended, so segments need no separate tail path.
 //
 // Shared memory.  The recent words sit in four interleaved sub-buffers of P
@@ -27,7 +28,7 @@ namespace mtgp {
 namespace {
 
 struct WideCtx {
-    uint32_t N, S, mask, sh1, sh2, P;
+    uint32_t N, S, R, mask, sh1, sh2, P;   // R: words per round, R <= S
     uint32_t rec_r, tmp_r, tmpf_r;      // this lane's table entries (index lane & 15)
     // byte offsets (the same for every thread) of the words at linear
     // positions 4q - N + k and 4q - S - 1 + k (k = 0 .. 4), and 4q + j
@@ -155,7 +156,7 @@ __device__ __forceinline__ bool wide_segment(const WideCtx &g, uint32_t *X, uint
                                              uint32_t *out)
 {
     while (n > 0u) {
-        const uint32_t nr = (uint32_t)min((uint64_t)g.S, n);
+        const uint32_t nr = (uint32_t)min((uint64_t)g.R, n);
         if (rel + g.N + nr + 8u > cap) {                     // compaction: live words to the front
             const uint32_t to = 4u + (rel & 3u);
             if (to + g.N > rel) return false;                // buffer too small (checked by the host)
@@ -193,6 +194,7 @@ __global__ void __launch_bounds__(T, (QW == 1 ? 960 : 640) / T) k_wide(const Lau
         WideCtx g;
         g.N = gd.N;
         g.S = gd.N - gd.M;
+        g.R = a.round_words && a.round_words < g.S ? a.round_words : g.S;   // words per round
         g.mask = gd.mask;
         g.sh1 = gd.sh1;
         g.sh2 = gd.sh2;

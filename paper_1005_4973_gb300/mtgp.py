@@ -35,6 +35,19 @@ def mtgp_params_search(mexp: int, seed0: int, gen_id: int, max_tries: int = 1 <<
     return p, found.value, tries.value, poly_from_words(words, mexp)
 
 
+def mtgp_params_search_gpu(mexp: int, seed0: int, gen_id: int, max_tries: int = 1 << 20, threads: int = 0,
+                           stream=None):
+    """The Sec. 5 recursion-parameter search with Berlekamp-Massey on the GPU
+    (one warp per candidate); the same result as mtgp_params_search."""
+    p = mtgp_params()
+    found, tries = ctypes.c_uint64(), ctypes.c_uint64()
+    words = np.zeros(mexp // 64 + 1, dtype=np.uint64)
+    L.check(L.LIB.mtgp_params_search_gpu(mexp, seed0, gen_id, max_tries, threads, L.stream_handle(stream),
+                                         ctypes.byref(p), ctypes.byref(found), ctypes.byref(tries),
+                                         words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), words.size))
+    return p, found.value, tries.value, poly_from_words(words, mexp)
+
+
 def mtgp_params_equidistribution(p: mtgp_params, threads: int = 0):
     """k(v) for v = 1..32 (index v - 1) and the total dimension defect
     (Sec. 3.4, 3.8) of a full-period parameter set."""
@@ -173,12 +186,14 @@ class Pool:
         L.check(L.LIB.mtgp_pool_set_config(self.handle, ctypes.byref(c)))
         return c
 
-    def autotune(self, reqs, scratch, stream=None):
+    def autotune(self, reqs, scratch, stream=None, layouts: int = 1):
+        """The autotuner (mtgp_autotune): sets and returns (config, ms, layout);
+        layouts: bit 0 blocked, bit 1 interleaved allowed."""
         arr = L.requests_array(reqs)
-        best, ms = mtgp_config(), ctypes.c_float()
-        L.check(L.LIB.mtgp_autotune(self.handle, arr, len(reqs), L.ptr(scratch), L.stream_handle(stream),
-                                    ctypes.byref(best), ctypes.byref(ms)))
-        return best, ms.value
+        best, ms, lay = mtgp_config(), ctypes.c_float(), ctypes.c_int()
+        L.check(L.LIB.mtgp_autotune(self.handle, arr, len(reqs), L.ptr(scratch), layouts, L.stream_handle(stream),
+                                    ctypes.byref(best), ctypes.byref(lay), ctypes.byref(ms)))
+        return best, ms.value, lay.value
 
     # -- state --------------------------------------------------------------
     def position(self, i: int) -> int:
@@ -211,6 +226,10 @@ class Pool:
         v = ctypes.c_uint64()
         L.check(L.LIB.mtgp_pool_launch_count(self.handle, ctypes.byref(v)))
         return v.value
+
+    def set_spin_limit(self, polls: int) -> None:
+        """Flow form: polls per bounded wait (0 = default)."""
+        L.check(L.LIB.mtgp_pool_set_spin_limit(self.handle, polls))
 
     def set_timing(self, entries: int) -> None:
         """Record CUDA events around the jump and generation launches of the next calls."""

@@ -247,8 +247,9 @@ def test_autotune_leaves_streams_untouched_and_keeps_parity():
     reqs, total = _blocked([(0, 0, 200000), (1, 2, 150000), (2, 1, 90000)])
     pool = lib_pool(gens)
     scratch = torch.zeros(total, dtype=torch.int32, device="cuda")
-    best, ms = pool.autotune(reqs, scratch)
-    assert ms > 0 and best.threads in (32, 64, 128, 256, 512, 1024) and best.pieces in (0, 1)
+    best, ms, layout = pool.autotune(reqs, scratch)
+    assert ms > 0 and best.threads in (32, 64, 96, 128, 192, 256, 512, 1024) and best.pieces in (0, 1)
+    assert layout == 0 and best.form in (0, 1, 2, 3, 4)
     assert [pool.position(g) for g in range(3)] == [0, 0, 0]
     out = torch.zeros(total, dtype=torch.int32, device="cuda")
     pool.generate(reqs, out)
@@ -290,3 +291,30 @@ def test_pool_call_on_a_stream_under_capture_is_refused():
     fresh = lib_pool(gens)                           # a launch right after reports itself only
     fresh.generate(reqs, out)
     torch.cuda.synchronize()
+
+
+def test_autotune_picks_a_layout_and_the_output_follows_it():
+    """With the interleaved layout allowed (equal lengths, distinct
+    generators) the autotuner returns the layout it timed fastest, with its
+    chunk in the configuration; generating in that layout equals the oracle."""
+    gens = _gens([11213, 11213, 23209, 11213])
+    n = 1 << 16
+    reqs = [(g, g % 3, n, g * n) for g in range(4)]
+    pool = lib_pool(gens)
+    scratch = torch.zeros(4 * n, dtype=torch.int32, device="cuda")
+    best, ms, layout = pool.autotune(reqs, scratch, layouts=3)
+    assert layout in (0, 1) and ms > 0
+    assert [pool.position(g) for g in range(4)] == [0, 0, 0, 0]
+    out = torch.zeros(4 * n, dtype=torch.int32, device="cuda")
+    pool.generate(reqs, out, layout=layout)
+    torch.cuda.synchronize()
+    o = as_u32(out)
+    c = best.chunk
+    for j, (g, dt, nn, off) in enumerate(reqs):
+        p, st = oracle_state(gens[g])
+        ref = O.generate(p, st, nn, dt)
+        if layout == 0:
+            assert np.array_equal(o[off:off + nn], ref)
+        else:
+            idx = np.arange(nn)
+            assert np.array_equal(o[(idx // c) * (4 * c) + j * c + idx % c], ref)

@@ -486,3 +486,29 @@ def test_c4_batched_sampled():
         k = min(n, 1024)
         p, st = oracle_state(wl.gens[g])
         assert np.array_equal(as_u32(out[off:off + k]), O.generate(p, st, k, dt)), g
+
+
+def test_flow_form_bounded_wait_runs_out_and_reports():
+    """The flow form's waits between warps are bounded.  With a limit of two
+    polls some wait runs out: the launch still ends, bit 1 of the error word
+    (a wait ran out) comes back, and the next launch with the default limit
+    continues bit-exact on the same pool (the context stays usable)."""
+    g = [WL.GenSpec(11213, 1, 0, 0)]
+    pool = lib_pool(g)
+    pool.set_config(threads=256, form=2)
+    out = torch.zeros(1 << 18, dtype=torch.int32, device="cuda")
+    pool.set_spin_limit(2)
+    pool.generate([(0, 0, 1 << 18, 0)], out)
+    torch.cuda.synchronize()
+    assert pool.errors() & 2
+    pool.set_spin_limit(0)
+    p, st = oracle_state(g[0])
+    fresh = lib_pool(g)                                  # the failed call's state is unspecified
+    fresh.set_config(threads=256, form=2)
+    fresh.generate([(0, 1, 4097, 0)], out)
+    torch.cuda.synchronize()
+    assert fresh.errors() == 0
+    assert np.array_equal(as_u32(out)[:4097], O.generate(p, st, 4097, 1))
+    pool.generate([(0, 0, 1000, 0)], out)               # the first pool also runs again, without errors
+    torch.cuda.synchronize()
+    assert pool.errors() == 0

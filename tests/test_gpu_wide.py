@@ -227,3 +227,19 @@ def test_c2_instances_in_full():
     pool.generate(reqs, out)
     torch.cuda.synchronize()
     _check(gens, reqs, as_u32(out), pool)
+
+
+@pytest.mark.parametrize("round_words", [8, 12, 128, 256])
+def test_rounds_shorter_than_s(round_words):
+    """mtgp_config.round_words: the wide form runs rounds of fewer than S
+    words (any n <= S consecutive words are independent, Sec. 3.2); outputs
+    and states equal the oracle's, ragged segments of every residue."""
+    gens = [g for g in MIXED if _fits(g, 128)]
+    pool = lib_pool(gens)
+    pool.set_config(threads=128, form=3, round_words=round_words)
+    reqs, total = _ragged_requests(len(gens), 1000 + round_words)
+    out = torch.full((total + 8,), 0x5A, dtype=torch.int32, device="cuda")
+    pool.generate(reqs, out)
+    torch.cuda.synchronize()
+    _check(gens, reqs, as_u32(out), pool)
+    assert pool.errors() == 0

@@ -34,7 +34,7 @@ METRIC = "MTGP Gnum/s & HBM write GB/s vs peak (plain vs batched); served p50/p9
 KERNEL_SOURCES = ["paper_1005_4973_gb300/csrc/mtgp_device.cuh", "paper_1005_4973_gb300/csrc/mtgp_pairs.cuh",
                   "paper_1005_4973_gb300/csrc/mtgp_layout.h"]
 # generation kernel of each launch form (mtgp_config.form)
-FORM_KERNEL = {0: "k_generate", 1: "k_split", 2: "k_flow", 3: "k_wide", 4: "k_pairs"}
+FORM_KERNEL = {0: "k_generate", 1: "k_split", 2: "k_flow", 3: "k_wide", 4: "k_pairs", 5: "k_dual"}
 DTYPE = "u32+f32"       # integer recursion; f32 outputs by mantissa fill (one exact subtraction for [0,1))
 
 

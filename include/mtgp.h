@@ -99,14 +99,18 @@ typedef struct mtgp_request {
  * x_i of the next) and whose outputs leave in one 16-byte store; blocked
  * layouts only (interleaved calls run in the plain form).  Pair form: each
  * thread owns two adjacent columns per slot (x_{i+1} and one tempering word
- * shared within the pair, 8-byte stores), 128 threads.  On GB300 the plain
- * form measured fastest; mtgp_autotune tries every form. */
+ * shared within the pair, 8-byte stores), 128 threads.  Dual form: a block of
+ * 128 threads runs two work items at once, a round of each between block
+ * barriers, each in its own half of the shared buffer; every generator of a
+ * launch must have 257 <= S <= 384 (MTGP 11213), or the launch fails with
+ * MTGP_EINVAL.  mtgp_autotune tries every form. */
 typedef struct mtgp_config {
     uint32_t threads;          /* threads per block: plain 32, 64, 128, 256, 512
                                   (at most 11, 12, 11, 6, 8 columns per thread);
                                   split 128, 256, 512, 1024 (at most 12, 11, 6, 3);
                                   flow 128, 256, 512, 1024 (at most 12, 11, 6, 8);
-                                  wide 96, 128, 192 (rounds of at most 1529 words) */
+                                  wide 96, 128, 192 (rounds of at most 1529 words);
+                                  pairs 128 (at most 6 pairs); dual 128 (3)         */
     uint32_t persistent;       /* 1 (default): grid of SMs x blocks_per_sm blocks
                                   taking work items longest first from a device
                                   counter; 0: one block per work item               */
@@ -117,13 +121,17 @@ typedef struct mtgp_config {
     uint32_t chunk;            /* interleaved layout chunk, power of two >= 32       */
     uint32_t buffer_words;     /* shared-memory words per block, 0 = sized from the
                                   launch (>= 2N + owners ceil(S / owners) + 32 is
-                                  required, owners = threads or threads / 2; wide
+                                  required, owners = threads or threads / 2, twice
+                                  that for the dual form's two halves; wide
                                   form: 4 floor(buffer_words / 4) >= 2N + S + 24)    */
     uint32_t form;             /* 0 plain, 1 split (recursion and output warp groups
                                   handing rounds over through named barriers),
                                   2 flow (split groups, and each recursion warp
                                   waits only for the warps holding its inputs),
-                                  3 wide (4 adjacent columns per thread)            */
+                                  3 wide (4 adjacent columns per thread),
+                                  4 pairs (2 adjacent columns per thread),
+                                  5 dual (two items per block; always pulls
+                                  items from the work counter)                      */
     uint32_t pieces;           /* jump-ahead (Sec. 7): a generator's work in one call
                                   (blocked layout) may run as up to this many pieces
                                   on separate blocks, piece m starting from the state

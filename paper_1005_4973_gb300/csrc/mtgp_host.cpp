@@ -247,8 +247,8 @@ constexpr uint64_t kSeqCap = 256ull << 20;           // walk scratch words per l
 
 mtgp_status check_config(const mtgp_config &c)
 {
-    if (c.form > 4u)
-        return fail(MTGP_EINVAL, "form must be 0 (plain), 1 (split), 2 (flow), 3 (wide) or 4 (pairs)");
+    if (c.form > 5u)
+        return fail(MTGP_EINVAL, "form must be 0 (plain), 1 (split), 2 (flow), 3 (wide), 4 (pairs) or 5 (dual)");
     if (!threads_supported(c.threads, c.form))
         return fail(MTGP_EINVAL, "no kernel of form %u with %u threads per block", c.form, c.threads);
     if (c.persistent > 1u) return fail(MTGP_EINVAL, "persistent must be 0 or 1");
@@ -463,9 +463,9 @@ mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_
         smax = std::max(smax, g.N - g.M);
     }
     if (c.form == 3u) return launch_shape_wide(p, c, gens, n, items, nmax, smax, qmax_out, B_out);
-    // columns a slot covers: one per thread (plain), one per thread of the
-    // recursion half (split, flow), two per thread (pairs)
-    const uint32_t owners = c.form == 4u ? 2u * c.threads : c.form ? c.threads / 2u : c.threads;
+    // columns a slot covers: one per thread (plain, dual), one per thread of
+    // the recursion half (split, flow), two per thread (pairs)
+    const uint32_t owners = c.form == 4u ? 2u * c.threads : (c.form == 0u || c.form == 5u) ? c.threads : c.threads / 2u;
     const uint32_t qmax = kernel_slots(c.threads, c.form, (smax + owners - 1u) / owners);
     if (!qmax)
         return fail(MTGP_EINVAL, "no compiled kernel runs rounds of %u words with %u threads (form %u)", smax,
@@ -476,8 +476,13 @@ mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_
     for (size_t i = 0; i < n; ++i) {
         const DevGen &g = p->host_gens[gens[i]];
         const uint32_t S = g.N - g.M, nq = (S + owners - 1u) / owners;
+        if (c.form == 5u && nq != qmax)   // dual: every item runs the compiled slot count
+            return fail(MTGP_EINVAL, "form 5 runs rounds of %u .. %u words with %u threads; generator %u has %u",
+                        (qmax - 1u) * c.threads + 1u, qmax * c.threads, c.threads, gens[i], S);
         if (c.form == 2u)   // flow: epochs of at least N + S words between compactions
             need = std::max(need, 2u * g.N + 2u * S + 32u * nq + 32u);
+        else if (c.form == 5u)   // dual: two halves, each as the plain form's buffer
+            need = std::max(need, 2u * (2u * g.N + nq * owners + 32u));
         else                // plain / split: reads of the last column slot stay inside
             need = std::max(need, 2u * g.N + nq * owners + 32u);
     }
@@ -494,8 +499,9 @@ mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_
         }
         per_sm = std::max(per_sm, 1u);
         const uint32_t budget = std::min(57344u, (uint32_t)((227u * 1024u / per_sm - 1024u) / 4u));
-        B = std::min(2u * nmax + 32u * smax + 32u, budget);
-        B = std::max(B, std::min(need + smax, 57344u));
+        const uint32_t halves = c.form == 5u ? 2u : 1u;
+        B = std::min(halves * (2u * nmax + 32u * smax + 32u), budget);
+        B = std::max(B, std::min(need + halves * smax, 57344u));
         B = std::max(B, need);
     }
     if (c.form == 4u && !c.buffer_words) {
@@ -506,7 +512,7 @@ mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_
         if (2u * H < need) H += 32u;
         B = 2u * H;
     }
-    if (c.form == 4u) B &= ~1u;                               // the kernel uses 2 floor(B / 2) words
+    if (c.form == 4u || c.form == 5u) B &= ~1u;               // the kernel uses 2 floor(B / 2) words
     if (B < need) return fail(MTGP_EINVAL, "buffer_words %u below the minimum %u for this launch", B, need);
     if (B > 57344u) return fail(MTGP_EINVAL, "state too large for shared memory (%u words)", B);
     *qmax_out = qmax;
@@ -736,17 +742,18 @@ mtgp_status launch_plan(mtgp_pool *p, const Plan &plan, void *dev_out, cudaStrea
     // fewer work items than SMs: each block's round latency is the time, so
     // the kernel with interleaved round tails (where compiled)
     const bool interleave = plan.work.size() < (size_t)std::max(p->sm_count, 1);
-    bool persistent = c.persistent != 0u;
+    bool persistent = c.persistent != 0u || c.form == 5u;   // the dual form always pulls items
     if (persistent) {
         int occ = 0;
         CU(generate_occupancy(c.threads, c.form, qmax, B, &occ, interleave), "occupancy");
         if (occ < 1) return fail(MTGP_EINVAL, "configuration does not fit on an SM");
         const int per_sm = c.blocks_per_sm ? std::min<int>((int)c.blocks_per_sm, occ) : occ;
         // every item resident at once: one block per item, no work counter
-        if (!c.blocks_per_sm && plan.work.size() <= (size_t)per_sm * (size_t)p->sm_count)
+        if (!c.blocks_per_sm && c.form != 5u && plan.work.size() <= (size_t)per_sm * (size_t)p->sm_count)
             persistent = false;
         else {
             CU(cudaMemsetAsync(p->d_ctl, 0, sizeof(unsigned), s), "reset work counter");
+            if (c.form == 5u) grid = (grid + 1u) / 2u;      // two items per block
             grid = std::min<uint32_t>(grid, (uint32_t)(per_sm * p->sm_count));
         }
     }
@@ -1263,7 +1270,7 @@ mtgp_status mtgp_autotune(mtgp_pool *p, const mtgp_request *reqs, uint32_t nreq,
         // interleaved one, with the default chunk, if blocked is not allowed)
         std::vector<mtgp_config> cands;
         for (uint32_t pieces : {0u, 1u})
-            for (uint32_t form : {0u, 1u, 2u, 3u, 4u})
+            for (uint32_t form : {0u, 1u, 2u, 3u, 4u, 5u})
                 for (uint32_t threads : {32u, 64u, 96u, 128u, 192u, 256u, 512u, 1024u})
                     for (uint32_t rw : {0u, 128u, 256u})
                         for (uint32_t pers : {0u, 1u})

@@ -77,6 +77,7 @@ GenKernel wide_kernel(uint32_t threads, uint32_t qw);
 GenKernel pair_kernel_t128_q2();
 GenKernel pair_kernel_t128_q3();
 GenKernel pair_kernel_t128_q6();
+GenKernel dual_kernel_t128_q3();   // dual form (two items per block), rounds of 257 .. 384 words
 // Flow-form kernels: blocks of 2 W warps (W recursion + W output warps).
 GenKernel flow_kernel_w2(uint32_t cmax);
 GenKernel flow_kernel_w4(uint32_t cmax);

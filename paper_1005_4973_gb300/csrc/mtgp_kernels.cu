@@ -62,6 +62,7 @@ GenKernel pick(uint32_t threads, uint32_t form, uint32_t qmax, bool interleave =
         if (k) return k;
     }
     if (form == 3u) return wide_kernel(threads, qmax);
+    if (form == 5u) return threads == 128u && qmax == 3u ? dual_kernel_t128_q3() : nullptr;
     if (form == 4u) {
         if (threads == 128u) {
             switch (qmax) {

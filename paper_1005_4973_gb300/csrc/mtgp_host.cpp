@@ -579,20 +579,25 @@ mtgp_status split_plan(mtgp_pool *p, Plan *plan, cudaStream_t s)
         const DevGen &g = p->host_gens[dw.gen];
         // auto: a piece at least mexp N / 4 numbers long, so that its jump
         // (about 0.7 mexp N word operations) stays a few per cent of its work;
-        // when the work items do not fill the SMs, pieces down to 2^14 numbers
-        // (jumps then run on SMs that would otherwise idle, and a launch's time
-        // is one jump plus one piece)
-        const uint64_t lmin = c.piece_log2 ? min_piece
-                              : few ? (uint64_t)1u << 14
-                                    : std::max<uint64_t>(min_piece, (uint64_t)g.mexp * g.N / 4u);
-        if (dw.total < 2u * lmin) continue;
+        // when the work items do not fill the SMs, also pieces down to 2^14
+        // numbers, at most kfew per item (jumps then run on SMs that would
+        // otherwise idle, and a launch's time is one jump plus one piece) --
+        // whichever rule gives more pieces (long items in a launch of few
+        // items, 2^26 numbers of MTGP23209 each: 15 pieces, not 3)
+        const uint64_t lmin = c.piece_log2 ? min_piece : std::max<uint64_t>(min_piece, (uint64_t)g.mexp * g.N / 4u);
+        const uint64_t lfew = c.piece_log2 ? min_piece : (uint64_t)1u << 14;
+        const bool few_rule = !c.pieces && few;
+        if (dw.total < 2u * (few_rule ? std::min(lmin, lfew) : lmin)) continue;
         bool blocked = true;
         for (uint32_t q = 0; q < dw.seg_count; ++q)
             blocked = blocked && plan->segs[dw.seg_begin + q].chunk_log2 == kBlocked;
         if (!blocked) continue;
-        uint64_t k = std::min<uint64_t>(kt, dw.total / lmin);
-        if (Lt) k = std::min<uint64_t>(k, (dw.total + Lt - 1u) / Lt);
-        if (!c.pieces && few) k = std::min<uint64_t>(k, kfew);
+        const uint64_t kLt = Lt ? (dw.total + Lt - 1u) / Lt : ~0ull;
+        uint64_t k = std::min<uint64_t>({kt, dw.total / lmin, kLt});
+        if (few_rule) {
+            const uint64_t kf = std::min<uint64_t>({kt, dw.total / lfew, kLt, kfew});
+            k = c.piece_log2 ? std::min(k, kfew) : std::max(k, kf);
+        }
         if (k < 2u) continue;
         uint64_t L = (dw.total + k - 1u) / k;
         L = (L + 63u) & ~63ull;

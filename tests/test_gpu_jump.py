@@ -99,6 +99,35 @@ def test_pieces_across_segments_and_calls():
         assert pool.position(g) == sum(n for _, n, _ in hist[g])
 
 
+def test_automatic_pieces_of_long_items_in_a_launch_of_few_items():
+    """Fewer work items than SMs, each long enough for the normal piece rule
+    to give more pieces than the few-item rule (100 items of 5 x 2^20 + 777
+    numbers of MTGP11213: 5 pieces each, not 4): sampled generators' streams,
+    states and positions equal the oracle's, over two calls."""
+    n = 5 * (1 << 20) + 777
+    gens = _gens([11213] * 100)
+    pool = lib_pool(gens)
+    spec = [(g, g % 3, n) for g in range(100)]
+    reqs, total = _blocked(spec)
+    out = torch.full((total,), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    sample = (0, 1, 2, 37, 98, 99)
+    got = {g: [] for g in sample}
+    for _ in range(2):
+        pool.generate(reqs, out)
+        torch.cuda.synchronize()
+        o = as_u32(out)
+        for g in sample:
+            off = reqs[g][3]
+            got[g].append(o[off:off + n].copy())
+    assert pool.errors() == 0
+    for g in sample:
+        outs, st = oracle_stream(gens[g], [(g % 3, n), (g % 3, n)])
+        for mine, ref in zip(got[g], outs):
+            assert np.array_equal(mine, ref), g
+        assert np.array_equal(pool.read_state(g), st), g
+        assert pool.position(g) == 2 * n
+
+
 def test_split_and_unsplit_calls_interleave():
     gens = _gens([44497, 11213])
     pool = lib_pool(gens)

@@ -205,12 +205,15 @@ mtgp_status mtgp_params_search(uint32_t mexp, uint64_t seed0, uint32_t id, uint6
 
 /*
  * The same search (same candidates, same acceptance, same result) with the
- * Berlekamp-Massey step on the GPU: candidates run in batches of up to 4096;
- * the host cores draw them and walk their MSB sequences, one warp per
- * candidate finds the sequence's minimal polynomial on `stream`, and the
- * host cores test the ones of degree mexp for irreducibility in candidate
- * order.  Allocates and frees its device buffers (about 4096 x 3 mexp / 8
- * bytes); synchronous.  Errors as mtgp_params_search, plus MTGP_ECUDA.
+ * polynomial work on the GPU: candidates run in batches of up to 4096; the
+ * host cores draw them and walk their MSB sequences, one warp per candidate
+ * finds the sequence's minimal polynomial on `stream`, and one block per
+ * candidate of degree mexp tests it for irreducibility (the test of
+ * mtgp_f2_irreducible_gpu; the survivors of its sieve are squared on streams
+ * of the call's own while later batches run, and batches are settled in
+ * order).  mexp > 32.  Allocates and frees its device buffers and streams
+ * (about 4 x 4096 x mexp / 8 bytes); synchronous.  Errors as
+ * mtgp_params_search, plus MTGP_ECUDA.
  */
 mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uint32_t id, uint64_t max_tries,
                                    uint32_t threads, void *stream, mtgp_params *out, uint64_t *found_seed,
@@ -480,6 +483,18 @@ mtgp_status mtgp_pool_annihilator(mtgp_pool *p, uint32_t i, uint64_t *poly, uint
  *   mulmod:   a b mod m
  *   xpow_mod: x^e mod m */
 mtgp_status mtgp_f2_minpoly(const uint64_t *bits, uint64_t n, uint64_t *out, uint32_t out_words, int64_t *deg);
+/* Irreducibility over F2 on the GPU of `count` polynomials (host memory,
+ * `words` 64-bit words each in the layout above), the acceptance test of the
+ * Sec. 5 recursion search: verdicts[j] = 1 if polynomial j has degree exactly
+ * p and is irreducible, else 0.  p must be a prime > 32 (the test is
+ * Rabin's for prime degree: no root in F2 and x^(2^p) = x mod phi, after a
+ * gcd against the product of x^(2^k) - x for 10 < k <= 20 that rejects
+ * polynomials with a factor of degree <= 20); words >= p / 64 + 1.  One
+ * block per polynomial on `stream`; synchronous; the device buffers are
+ * allocated and freed by the call.  MTGP_EINVAL for NULL pointers, count 0,
+ * p not prime or too small, or too few words; MTGP_ENOMEM; MTGP_ECUDA. */
+mtgp_status mtgp_f2_irreducible_gpu(const uint64_t *polys, uint32_t count, uint32_t words, uint32_t p,
+                                    void *stream, uint8_t *verdicts);
 mtgp_status mtgp_f2_mulmod(const uint64_t *a, uint32_t a_words, const uint64_t *b, uint32_t b_words,
                            const uint64_t *m, uint32_t m_words, uint64_t *out, uint32_t out_words, int64_t *deg);
 mtgp_status mtgp_f2_xpow_mod(uint64_t e, const uint64_t *m, uint32_t m_words, uint64_t *out, uint32_t out_words,

@@ -123,6 +123,7 @@ _SIGS = {
     "mtgp_params_report": (ctypes.c_int, [_P(mtgp_params), _u32, ctypes.c_char_p, _sz]),
     "mtgp_params_record": (ctypes.c_int, [_P(mtgp_params), _P(_u64), _u32, _u32, ctypes.c_char_p, _sz]),
     "mtgp_f2_minpoly": (ctypes.c_int, [_P(_u64), _u64, _P(_u64), _u32, _P(ctypes.c_int64)]),
+    "mtgp_f2_irreducible_gpu": (ctypes.c_int, [_P(_u64), _u32, _u32, _u32, _vp, _P(ctypes.c_uint8)]),
     "mtgp_f2_mulmod": (ctypes.c_int, [_P(_u64), _u32, _P(_u64), _u32, _P(_u64), _u32, _P(_u64), _u32,
                                       _P(ctypes.c_int64)]),
     "mtgp_f2_xpow_mod": (ctypes.c_int, [_u64, _P(_u64), _u32, _P(_u64), _u32, _P(ctypes.c_int64)]),

@@ -21,7 +21,7 @@ NVCC = os.environ.get("NVCC", "nvcc")
 SOURCES = ["mtgp_kernels.cu", "mtgp_gen_t32.cu", "mtgp_gen_t64.cu", "mtgp_gen_t128.cu", "mtgp_gen_t256.cu",
            "mtgp_gen_t512.cu", "mtgp_split_rt64.cu", "mtgp_split_rt128.cu", "mtgp_split_rt256.cu",
            "mtgp_split_rt512.cu", "mtgp_flow_w2.cu", "mtgp_flow_w4.cu", "mtgp_flow_w8.cu",
-           "mtgp_flow_w16.cu", "mtgp_wide.cu", "mtgp_pairs_t128_q2.cu", "mtgp_pairs_t128_q3.cu", "mtgp_pairs_t128_q6.cu", "mtgp_dual_t128_q3.cu", "mtgp_noalloc.cu", "mtgp_jump.cu", "mtgp_bm.cu", "mtgp_host.cpp", "mtgp_jump_host.cpp",
+           "mtgp_flow_w16.cu", "mtgp_wide.cu", "mtgp_pairs_t128_q2.cu", "mtgp_pairs_t128_q3.cu", "mtgp_pairs_t128_q6.cu", "mtgp_dual_t128_q3.cu", "mtgp_noalloc.cu", "mtgp_jump.cu", "mtgp_bm.cu", "mtgp_irr.cu", "mtgp_host.cpp", "mtgp_jump_host.cpp",
            "mtgp_f2.cpp", "mtgp_search.cpp", "mtgp_equid.cpp",
            "mtgp_server.cpp"]
 

@@ -156,12 +156,21 @@ extern "C" mtgp_status mtgp_params_search(uint32_t mexp, uint64_t seed0, uint32_
     return MTGP_OK;
 }
 
-// The same search with the Berlekamp-Massey step on the GPU: candidates run in
-// batches; the host draws each candidate and walks its MSB sequence (threads
-// over candidates), one warp per candidate finds the sequence's minimal
-// polynomial (mtgp_bm.cu), and the host tests the ones of degree mexp for
-// irreducibility in candidate order (threads over candidates).  The first
-// accepted candidate is the host search's.
+// The same search with the polynomial work on the GPU.  Candidates run in
+// batches of up to 4096: the host draws each candidate and walks its MSB
+// sequence (threads over candidates), one warp per candidate finds the
+// sequence's minimal polynomial (mtgp_bm.cu), and one block per candidate of
+// degree mexp runs the irreducibility sieve (mtgp_irr.cu, stage 0) on the
+// caller's stream.  The few survivors' p squarings (stage 1) take far longer
+// than a batch's sieve, so they run on a stream of their own per batch (up to
+// kIrrSlots batches in flight) while later batches are walked and sieved;
+// batches are settled in order, so the first accepted candidate is the host
+// search's.
+namespace {
+constexpr uint32_t kIrrSieve = 20;   // factors of degree <= 20 found before the squarings
+constexpr uint32_t kIrrSlots = 4;    // batches whose squarings may run at once
+}  // namespace
+
 extern "C" mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uint32_t id, uint64_t max_tries,
                                               uint32_t threads, void *stream, mtgp_params *out,
                                               uint64_t *found_seed, uint64_t *tries, uint64_t *charpoly,
@@ -174,6 +183,7 @@ extern "C" mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uin
     mtgp_params probe;
     mtgp_status st = mtgp_params_draw(mexp, seed0, id, &probe);
     if (st != MTGP_OK) return st;
+    if (mexp < 33u) return (mtgp_status)report_error(MTGP_EINVAL, "search: the GPU search needs mexp > 32");
     const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
     const unsigned nt = threads ? threads : hw;
     const uint64_t n = 2ull * mexp;
@@ -181,11 +191,28 @@ extern "C" mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uin
     const uint32_t owords = mexp / 32u + 2u;
     const uint64_t batch = std::min<uint64_t>(4096u, max_tries);
     cudaStream_t s = (cudaStream_t)stream;
-    uint32_t *d_seq = nullptr, *d_out = nullptr, *d_len = nullptr;
+    struct Slot {
+        uint32_t *d_out = nullptr, *d_len = nullptr, *d_ver = nullptr, *h_ver = nullptr;
+        cudaStream_t sf = nullptr;
+        cudaEvent_t sieved = nullptr, settled = nullptr;
+        bool pending = false;
+        uint64_t base = 0, nb = 0;
+    };
+    Slot slot[kIrrSlots];
+    uint32_t *d_seq = nullptr;
     auto cleanup = [&] {
+        (void)cudaStreamSynchronize(s);
+        for (Slot &q : slot) {
+            if (q.sf) (void)cudaStreamSynchronize(q.sf);
+            cudaFree(q.d_out);
+            cudaFree(q.d_len);
+            cudaFree(q.d_ver);
+            cudaFreeHost(q.h_ver);
+            if (q.sieved) cudaEventDestroy(q.sieved);
+            if (q.settled) cudaEventDestroy(q.settled);
+            if (q.sf) cudaStreamDestroy(q.sf);
+        }
         cudaFree(d_seq);
-        cudaFree(d_out);
-        cudaFree(d_len);
         (void)cudaGetLastError();
     };
     auto cuda_err = [&](cudaError_t e, const char *what) {
@@ -195,27 +222,73 @@ extern "C" mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uin
         return (mtgp_status)report_error(e == cudaErrorMemoryAllocation ? MTGP_ENOMEM : MTGP_ECUDA, buf);
     };
     cudaError_t e = cudaMalloc(&d_seq, (size_t)batch * words * 4u);
-    if (e == cudaSuccess) e = cudaMalloc(&d_out, (size_t)batch * owords * 4u);
-    if (e == cudaSuccess) e = cudaMalloc(&d_len, (size_t)batch * 4u);
-    if (e != cudaSuccess) return cuda_err(e, "cudaMalloc");
+    for (Slot &q : slot) {
+        if (e == cudaSuccess) e = cudaMalloc(&q.d_out, (size_t)batch * owords * 4u);
+        if (e == cudaSuccess) e = cudaMalloc(&q.d_len, (size_t)batch * 4u);
+        if (e == cudaSuccess) e = cudaMalloc(&q.d_ver, (size_t)batch * 4u);
+        if (e == cudaSuccess) e = cudaHostAlloc(&q.h_ver, (size_t)batch * 4u, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q.sf, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.sieved, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.settled, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_err(e, "allocation");
+    // Settles the batch in slot q (waits for its squarings): the index of its
+    // first accepted candidate, or UINT64_MAX.
+    auto settle = [&](Slot &q, uint64_t *j_out) -> cudaError_t {
+        *j_out = std::numeric_limits<uint64_t>::max();
+        if (!q.pending) return cudaSuccess;
+        q.pending = false;
+        const cudaError_t r = cudaEventSynchronize(q.settled);
+        if (r != cudaSuccess) return r;
+        for (uint64_t j = 0; j < q.nb; ++j)
+            if (q.h_ver[j] == 1u) {
+                *j_out = j;
+                break;
+            }
+        return cudaSuccess;
+    };
+    // Reports the accepted candidate j of slot q.
+    auto accept = [&](Slot &q, uint64_t j) -> mtgp_status {
+        std::vector<uint32_t> poly(owords);
+        cudaError_t r = cudaMemcpy(poly.data(), q.d_out + (size_t)j * owords, (size_t)owords * 4u,
+                                   cudaMemcpyDeviceToHost);
+        if (r != cudaSuccess) return cuda_err(r, "copy of the accepted polynomial");
+        const uint64_t cand = q.base + j;
+        cleanup();
+        const mtgp_status r2 = mtgp_params_draw(mexp, seed0 + cand, id, out);
+        if (r2 != MTGP_OK) return r2;
+        *found_seed = seed0 + cand;
+        *tries = cand + 1u;
+        if (charpoly) {
+            std::memset(charpoly, 0, sizeof(uint64_t) * charpoly_words);
+            for (uint32_t b = 0; b <= mexp; ++b)
+                if ((poly[b >> 5] >> (b & 31u)) & 1u) charpoly[b >> 6] |= 1ull << (b & 63u);
+        }
+        return MTGP_OK;
+    };
     try {
         std::vector<uint64_t> seq((size_t)batch * w64);
-        std::vector<uint32_t> polys((size_t)batch * owords), lens(batch);
-        for (uint64_t base = 0; base < max_tries; base += batch) {
+        uint64_t bi = 0;
+        for (uint64_t base = 0; base < max_tries; base += batch, ++bi) {
+            Slot &q = slot[bi % kIrrSlots];
+            uint64_t j = 0;
+            e = settle(q, &j);                                    // the batch kIrrSlots back, in order
+            if (e != cudaSuccess) return cuda_err(e, "irreducibility squarings");
+            if (j != std::numeric_limits<uint64_t>::max()) return accept(q, j);
             const uint64_t nb = std::min<uint64_t>(batch, max_tries - base);
             std::atomic<uint64_t> next{0};
             std::atomic<bool> bad{false};
             auto walker = [&] {
                 try {
                     std::vector<uint64_t> bits;
-                    for (uint64_t j; (j = next.fetch_add(1)) < nb;) {
+                    for (uint64_t t; (t = next.fetch_add(1)) < nb;) {
                         mtgp_params p;
-                        if (mtgp_params_draw(mexp, seed0 + base + j, id, &p) != MTGP_OK) {
+                        if (mtgp_params_draw(mexp, seed0 + base + t, id, &p) != MTGP_OK) {
                             bad = true;
                             return;
                         }
-                        msb_sequence(p, 12345u + base + j, n, bits);
-                        std::copy(bits.begin(), bits.begin() + w64, seq.begin() + (ptrdiff_t)(j * w64));
+                        msb_sequence(p, 12345u + base + t, n, bits);
+                        std::copy(bits.begin(), bits.begin() + w64, seq.begin() + (ptrdiff_t)(t * w64));
                     }
                 } catch (const std::exception &) {
                     bad = true;
@@ -229,57 +302,27 @@ extern "C" mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uin
                 return (mtgp_status)report_error(MTGP_ENOMEM, "search: host allocation failed");
             }
             e = cudaMemcpyAsync(d_seq, seq.data(), (size_t)nb * w64 * 8u, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = launch_bm(d_seq, (uint32_t)nb, (uint32_t)n, words, d_out, owords, d_len, s);
+            if (e == cudaSuccess) e = launch_bm(d_seq, (uint32_t)nb, (uint32_t)n, words, q.d_out, owords, q.d_len, s);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(lens.data(), d_len, (size_t)nb * 4u, cudaMemcpyDeviceToHost, s);
+                e = launch_irr(q.d_out, (uint32_t)nb, owords, q.d_len, mexp, kIrrSieve, 0u, q.d_ver, s);
+            if (e == cudaSuccess) e = cudaEventRecord(q.sieved, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(q.sf, q.sieved, 0);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(polys.data(), d_out, (size_t)nb * owords * 4u, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) return cuda_err(e, "Berlekamp-Massey batch");
-            // candidates of degree mexp, in order; the smallest irreducible wins
-            std::vector<uint64_t> cand;
-            for (uint64_t j = 0; j < nb; ++j)
-                if (lens[j] == mexp) cand.push_back(j);
-            std::atomic<size_t> ci{0};
-            std::atomic<uint64_t> best{std::numeric_limits<uint64_t>::max()};
-            auto tester = [&] {
-                try {
-                    for (size_t i; (i = ci.fetch_add(1)) < cand.size();) {
-                        const uint64_t j = cand[i];
-                        if (j >= best.load()) return;
-                        f2::Poly phi((size_t)(mexp / 64u) + 1u, 0u);
-                        for (uint32_t b = 0; b <= mexp; ++b)
-                            if ((polys[(size_t)j * owords + (b >> 5)] >> (b & 31u)) & 1u)
-                                phi[b >> 6] |= 1ull << (b & 63u);
-                        if (!irreducible_prime_degree(phi, mexp, 40u)) continue;
-                        uint64_t b0 = best.load();
-                        while (j < b0 && !best.compare_exchange_weak(b0, j)) {
-                        }
-                    }
-                } catch (const std::exception &) {
-                    bad = true;
-                }
-            };
-            pool.clear();
-            for (unsigned t = 0; t < nt; ++t) pool.emplace_back(tester);
-            for (auto &th : pool) th.join();
-            if (bad) {
-                cleanup();
-                return (mtgp_status)report_error(MTGP_ENOMEM, "search: host allocation failed");
-            }
-            const uint64_t j = best.load();
-            if (j == std::numeric_limits<uint64_t>::max()) continue;
-            cleanup();
-            st = mtgp_params_draw(mexp, seed0 + base + j, id, out);
-            if (st != MTGP_OK) return st;
-            *found_seed = seed0 + base + j;
-            *tries = base + j + 1u;
-            if (charpoly) {
-                std::memset(charpoly, 0, sizeof(uint64_t) * charpoly_words);
-                for (uint32_t b = 0; b <= mexp; ++b)
-                    if ((polys[(size_t)j * owords + (b >> 5)] >> (b & 31u)) & 1u) charpoly[b >> 6] |= 1ull << (b & 63u);
-            }
-            return MTGP_OK;
+                e = launch_irr(q.d_out, (uint32_t)nb, owords, q.d_len, mexp, kIrrSieve, 1u, q.d_ver, q.sf);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(q.h_ver, q.d_ver, (size_t)nb * 4u, cudaMemcpyDeviceToHost, q.sf);
+            if (e == cudaSuccess) e = cudaEventRecord(q.settled, q.sf);
+            if (e != cudaSuccess) return cuda_err(e, "Berlekamp-Massey and irreducibility batch");
+            q.pending = true;
+            q.base = base;
+            q.nb = nb;
+        }
+        for (uint64_t k = 0; k < kIrrSlots; ++k) {                // the batches still in flight, in order
+            Slot &q = slot[(bi + k) % kIrrSlots];
+            uint64_t j = 0;
+            e = settle(q, &j);
+            if (e != cudaSuccess) return cuda_err(e, "irreducibility squarings");
+            if (j != std::numeric_limits<uint64_t>::max()) return accept(q, j);
         }
     } catch (const std::exception &) {
         cleanup();
@@ -287,4 +330,50 @@ extern "C" mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uin
     }
     cleanup();
     return (mtgp_status)report_error(MTGP_EINVAL, "search: no full-period set within max_tries");
+}
+
+// Irreducibility of host polynomials of prime degree p on the GPU (the
+// search's acceptance test, for callers and tests).
+extern "C" mtgp_status mtgp_f2_irreducible_gpu(const uint64_t *polys, uint32_t count, uint32_t words, uint32_t p,
+                                               void *stream, uint8_t *verdicts)
+{
+    using namespace mtgp;
+    if (!polys || !verdicts || count == 0)
+        return (mtgp_status)report_error(MTGP_EINVAL, "irreducible: NULL pointer or count 0");
+    bool prime = p > 32u;
+    for (uint32_t d = 2; prime && (uint64_t)d * d <= p; ++d) prime = p % d != 0u;
+    if (!prime) return (mtgp_status)report_error(MTGP_EINVAL, "irreducible: p must be a prime > 32");
+    if (words < p / 64u + 1u) return (mtgp_status)report_error(MTGP_EINVAL, "irreducible: words < p / 64 + 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *d_polys = nullptr, *d_ver = nullptr;
+    auto fail_cuda = [&](cudaError_t e, const char *what) {
+        cudaFree(d_polys);
+        cudaFree(d_ver);
+        (void)cudaGetLastError();
+        char buf[200];
+        snprintf(buf, sizeof buf, "irreducible: %s: %s", what, cudaGetErrorString(e));
+        return (mtgp_status)report_error(e == cudaErrorMemoryAllocation ? MTGP_ENOMEM : MTGP_ECUDA, buf);
+    };
+    // 64-bit little-endian words are pairs of 32-bit words in the same order
+    const size_t bytes = (size_t)count * words * 8u;
+    cudaError_t e = cudaMalloc(&d_polys, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ver, (size_t)count * 4u);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    try {
+        std::vector<uint32_t> ver(count);
+        e = cudaMemcpyAsync(d_polys, polys, bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_irr(d_polys, count, 2u * words, nullptr, p, kIrrSieve, 0u, d_ver, s);
+        if (e == cudaSuccess) e = launch_irr(d_polys, count, 2u * words, nullptr, p, kIrrSieve, 1u, d_ver, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ver.data(), d_ver, (size_t)count * 4u, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail_cuda(e, "test");
+        for (uint32_t j = 0; j < count; ++j) verdicts[j] = ver[j] ? 1u : 0u;
+    } catch (const std::exception &) {
+        cudaFree(d_polys);
+        cudaFree(d_ver);
+        return (mtgp_status)report_error(MTGP_ENOMEM, "irreducible: host allocation failed");
+    }
+    cudaFree(d_polys);
+    cudaFree(d_ver);
+    return MTGP_OK;
 }

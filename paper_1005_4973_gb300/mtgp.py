@@ -129,6 +129,24 @@ def mtgp_f2_minpoly(bits) -> np.ndarray:
     return poly_from_words(out, d.value)
 
 
+def mtgp_f2_irreducible_gpu(polys, p: int, stream=None) -> np.ndarray:
+    """GPU irreducibility test (degree exactly p, p a prime > 32) of each
+    coefficient array in polys; returns a bool array."""
+    words = p // 64 + 1
+    arr = np.zeros((len(polys), words), dtype=np.uint64)
+    for j, c in enumerate(polys):
+        w = poly_to_words(c)
+        if w.size > words:
+            if np.any(w[words:]):
+                raise ValueError("polynomial of degree above p")
+            w = w[:words]
+        arr[j, :w.size] = w
+    ver = np.zeros(len(polys), dtype=np.uint8)
+    L.check(L.LIB.mtgp_f2_irreducible_gpu(_u64p(arr), len(polys), words, p, L.stream_handle(stream),
+                                          ver.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+    return ver.astype(bool)
+
+
 def mtgp_f2_mulmod(a, b, m) -> np.ndarray:
     aw, bw, mw = poly_to_words(a), poly_to_words(b), poly_to_words(m)
     out = np.zeros(mw.size + 1, dtype=np.uint64)

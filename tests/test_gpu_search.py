@@ -1,8 +1,12 @@
-"""The MTGPDC recursion search (Sec. 5) with Berlekamp-Massey on the GPU (one
-warp per candidate) against the host search and the oracle's search: the same
-first accepted candidate, and a characteristic polynomial equal to the
-oracle's Berlekamp-Massey polynomial of the set's MSB sequence, which
-annihilates the oracle's outputs."""
+"""The MTGPDC recursion search (Sec. 5) with its polynomial work on the GPU
+(Berlekamp-Massey, one warp per candidate; irreducibility, one block per
+candidate) against the host search and the oracle's search: the same first
+accepted candidate, and a characteristic polynomial equal to the oracle's
+Berlekamp-Massey polynomial of the set's MSB sequence.  The GPU
+irreducibility test alone against the oracle's plain test (x^(2^p) = x mod
+phi, no sieve) on irreducible trinomials, searched characteristic
+polynomials, random polynomials and products with factors of every small
+degree."""
 import time
 
 import numpy as np
@@ -44,13 +48,71 @@ def test_gpu_search_limits(M):
 
 
 def test_gpu_search_mtgp11213_timed(M):
-    """A full-size MTGP11213 search: the same set as the host search; both
-    times are printed (pytest -s)."""
+    """A full-size MTGP11213 search: the same set as the host search, and
+    faster; both times are printed (pytest -s)."""
     t0 = time.perf_counter()
     pg, sg, tg, phig = M.mtgp_params_search_gpu(11213, 1, 0)
     tgpu = time.perf_counter() - t0
     t0 = time.perf_counter()
     ph, sh, th, phih = M.mtgp_params_search(11213, 1, 0)
     thost = time.perf_counter() - t0
-    print(f"MTGP11213 search: GPU Berlekamp-Massey {tgpu:.2f} s, host {thost:.2f} s, {tg} candidates")
+    print(f"MTGP11213 search: GPU {tgpu:.2f} s, host {thost:.2f} s, {tg} candidates")
     assert sg == sh and np.array_equal(phig, phih) and phig.size - 1 == 11213
+    assert tgpu < thost
+
+
+# irreducible trinomials x^p + x^k + 1 of Mersenne exponents p
+TRINOMIALS = {89: 38, 127: 1, 521: 32, 607: 105, 1279: 216}
+
+
+def _poly(p, rng, odd_weight=True):
+    c = rng.integers(0, 2, size=p + 1).astype(np.uint8)
+    c[0] = c[p] = 1
+    if odd_weight and c.sum() % 2 == 0:
+        c[1 + int(rng.integers(0, p - 1))] ^= 1
+    return c
+
+
+@pytest.mark.parametrize("p", [37, 89, 107, 127, 521, 607, 1279])
+def test_gpu_irreducibility_equals_the_oracle(M, p):
+    rng = np.random.default_rng(p)
+    polys = []
+    if p in TRINOMIALS:
+        c = np.zeros(p + 1, dtype=np.uint8)
+        c[0] = c[TRINOMIALS[p]] = c[p] = 1
+        polys.append(c)
+    if p >= 89:
+        polys.append(M.mtgp_params_search(p, 1000, 7)[3])      # a searched characteristic polynomial
+    known = len(polys)                                        # the polynomials above are irreducible
+    nrand = 160 if p <= 127 else 24
+    polys += [_poly(p, rng) for _ in range(nrand)]
+    # products with a factor of each degree 2 .. 45 (the sieve finds those of degree <= 20)
+    for d in [d for d in (range(2, 46) if p <= 607 else (2, 17, 40, 41, 45)) if d < p - 1]:
+        f, g = _poly(d, rng, False), _poly(p - d, rng, False)
+        polys.append((np.convolve(f, g) % 2).astype(np.uint8))
+    # degree below p, even weight, no constant term
+    low = _poly(p, rng)
+    low[p] = 0
+    polys.append(low)
+    even = _poly(p, rng)
+    even[1 + int(np.nonzero(even[1:p])[0][0])] ^= 1
+    polys.append(even)
+    noc = _poly(p, rng)
+    noc[0] = 0
+    polys.append(noc)
+    got = M.mtgp_f2_irreducible_gpu(polys, p)
+    ref = np.array([O.irreducible_prime_degree(c) if c[p] else False for c in polys])
+    assert np.array_equal(got, ref), np.nonzero(got != ref)[0]
+    assert got[:known].all()
+    assert not got[-3:].any()
+
+
+def test_gpu_irreducibility_rejects_bad_arguments(M):
+    c = np.zeros(90, dtype=np.uint8)
+    c[0] = c[89] = 1
+    with pytest.raises(M.MTGPError):
+        M.mtgp_f2_irreducible_gpu([c], 91)                 # not prime
+    with pytest.raises(M.MTGPError):
+        M.mtgp_f2_irreducible_gpu([c[:32]], 31)            # too small
+    with pytest.raises(M.MTGPError):
+        M.mtgp_f2_irreducible_gpu([], 89)                  # no polynomial

@@ -196,8 +196,9 @@ mtgp_status mtgp_params_validate(const mtgp_params *p);
  * word j/64 = coefficient of x^j; charpoly_words >= mexp / 64 + 1).
  * threads = 0 uses every host core.  MTGP_EINVAL if none of max_tries
  * candidates qualifies.  The tempering table of the result is the drawn one;
- * mtgp_params_temper_search replaces it by the search of Sec. 5.  6-9 s of 16
- * cores for mexp 11213; the cost grows roughly as mexp^3.
+ * mtgp_params_temper_search replaces it by the search of Sec. 5.  For mexp
+ * 11213 (seed0 1, 14229 candidates) about 24 s of 16 cores; the cost grows
+ * roughly as mexp^3.  mtgp_params_search_gpu gives the same result faster.
  */
 mtgp_status mtgp_params_search(uint32_t mexp, uint64_t seed0, uint32_t id, uint64_t max_tries, uint32_t threads,
                                mtgp_params *out, uint64_t *found_seed, uint64_t *tries, uint64_t *charpoly,
@@ -488,8 +489,8 @@ mtgp_status mtgp_f2_minpoly(const uint64_t *bits, uint64_t n, uint64_t *out, uin
  * Sec. 5 recursion search: verdicts[j] = 1 if polynomial j has degree exactly
  * p and is irreducible, else 0.  p must be a prime > 32 (the test is
  * Rabin's for prime degree: no root in F2 and x^(2^p) = x mod phi, after a
- * gcd against the product of x^(2^k) - x for 10 < k <= 20 that rejects
- * polynomials with a factor of degree <= 20); words >= p / 64 + 1.  One
+ * gcd against the product of x^(2^k) - x for 20 < k <= 40 that rejects
+ * polynomials with a factor of degree <= 40); words >= p / 64 + 1.  One
  * block per polynomial on `stream`; synchronous; the device buffers are
  * allocated and freed by the call.  MTGP_EINVAL for NULL pointers, count 0,
  * p not prime or too small, or too few words; MTGP_ENOMEM; MTGP_ECUDA. */

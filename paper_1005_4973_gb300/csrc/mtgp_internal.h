@@ -96,9 +96,10 @@ cudaError_t launch_bm(const uint32_t *seq, uint32_t nseq, uint32_t n, uint32_t w
 // (bit j = coefficient of x^j), their degrees in deg (nullptr: from the
 // words).  Stage 0 (sieve: degree, roots, factors of degree <= K by a gcd)
 // sets verdict[j] = 0 (reducible) or 2 (survivor); stage 1 (the p squarings
-// of the survivors) turns each 2 into 1 (irreducible) or 0.
+// of the survivors) turns each 2 into 1 (irreducible) or 0, or into 0 early
+// once *abort (mapped host memory, nullptr for none) is nonzero.
 cudaError_t launch_irr(const uint32_t *polys, uint32_t count, uint32_t words, const uint32_t *deg, uint32_t p,
-                       uint32_t K, uint32_t stage, uint32_t *verdict, cudaStream_t s);
+                       uint32_t K, uint32_t stage, const uint32_t *abort, uint32_t *verdict, cudaStream_t s);
 
 // Records msg as the calling thread's last error and returns status.
 int report_error(int status, const char *msg);

@@ -203,12 +203,15 @@ __device__ void blk_copy(uint32_t *dst, const uint32_t *src, uint32_t n)
 // each; deg: their degrees (nullptr: read from the words).  Stage 0 (the
 // sieve) sets verdict[j] = 0 for a polynomial found reducible (degree other
 // than p, a root, a factor of degree <= K) and kSurvivor otherwise; stage 1
-// runs the p squarings for the survivors and sets 1 (irreducible) or 0.
+// runs the p squarings for the survivors and sets 1 (irreducible) or 0.  A
+// nonzero *abort (host memory the caller may set while stage 1 runs; nullptr
+// for none) ends stage 1 early, every 32 squarings, with verdict 0.
 constexpr uint32_t kSurvivor = 2u;
 
 __global__ void __launch_bounds__(kIrrThreads, 2) k_irr(const uint32_t *__restrict__ polys, uint32_t words,
                                                      const uint32_t *__restrict__ deg, uint32_t p, uint32_t K,
-                                                     uint32_t stage, uint32_t *__restrict__ verdict)
+                                                     uint32_t stage, const uint32_t *abort,
+                                                     uint32_t *__restrict__ verdict)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t tid = threadIdx.x, j = blockIdx.x;
@@ -264,7 +267,16 @@ __global__ void __launch_bounds__(kIrrThreads, 2) k_irr(const uint32_t *__restri
     }
     __syncthreads();
     if (stage == 1u) {                                           // x^(2^p) = x mod phi
+        __shared__ uint32_t s_abort;
         for (uint32_t k = 1; k <= p; ++k) {
+            if (abort && (k & 31u) == 0u) {
+                if (tid == 0) s_abort = *(volatile const uint32_t *)abort;
+                __syncthreads();
+                if (s_abort) {                                   // uniform: read after the barrier
+                    if (tid == 0) verdict[j] = 0u;
+                    return;
+                }
+            }
             blk_square(S, S.r);
             blk_reduce(S, S.t, 2 * (int)p - 2, S.phi, p, true);
             blk_copy(S.r, S.t, W);
@@ -327,7 +339,7 @@ size_t irr_smem_bytes(uint32_t p)
 }
 
 cudaError_t launch_irr(const uint32_t *polys, uint32_t count, uint32_t words, const uint32_t *deg, uint32_t p,
-                       uint32_t K, uint32_t stage, uint32_t *verdict, cudaStream_t s)
+                       uint32_t K, uint32_t stage, const uint32_t *abort, uint32_t *verdict, cudaStream_t s)
 {
     if (count == 0) return cudaSuccess;
     if (p < 33u || words < p / 32u + 1u || stage > 1u) return cudaErrorInvalidValue;
@@ -335,7 +347,7 @@ cudaError_t launch_irr(const uint32_t *polys, uint32_t count, uint32_t words, co
     cudaError_t e = raise_smem_limit((const void *)k_irr, smem);
     if (e != cudaSuccess) return e;
     clear_stale_error();
-    k_irr<<<count, kIrrThreads, smem, s>>>(polys, words, deg, p, K, stage, verdict);
+    k_irr<<<count, kIrrThreads, smem, s>>>(polys, words, deg, p, K, stage, abort, verdict);
     return cudaGetLastError();
 }
 

@@ -167,7 +167,7 @@ extern "C" mtgp_status mtgp_params_search(uint32_t mexp, uint64_t seed0, uint32_
 // batches are settled in order, so the first accepted candidate is the host
 // search's.
 namespace {
-constexpr uint32_t kIrrSieve = 20;   // factors of degree <= 20 found before the squarings
+constexpr uint32_t kIrrSieve = 40;   // factors of degree <= 40 found before the squarings
 constexpr uint32_t kIrrSlots = 4;    // batches whose squarings may run at once
 }  // namespace
 
@@ -200,7 +200,9 @@ extern "C" mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uin
     };
     Slot slot[kIrrSlots];
     uint32_t *d_seq = nullptr;
+    uint32_t *h_abort = nullptr, *d_abort = nullptr;   // set once the result is known: later squarings stop
     auto cleanup = [&] {
+        if (h_abort) *(volatile uint32_t *)h_abort = 1u;
         (void)cudaStreamSynchronize(s);
         for (Slot &q : slot) {
             if (q.sf) (void)cudaStreamSynchronize(q.sf);
@@ -213,6 +215,7 @@ extern "C" mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uin
             if (q.sf) cudaStreamDestroy(q.sf);
         }
         cudaFree(d_seq);
+        if (h_abort) cudaFreeHost(h_abort);
         (void)cudaGetLastError();
     };
     auto cuda_err = [&](cudaError_t e, const char *what) {
@@ -222,6 +225,11 @@ extern "C" mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uin
         return (mtgp_status)report_error(e == cudaErrorMemoryAllocation ? MTGP_ENOMEM : MTGP_ECUDA, buf);
     };
     cudaError_t e = cudaMalloc(&d_seq, (size_t)batch * words * 4u);
+    if (e == cudaSuccess) e = cudaHostAlloc(&h_abort, sizeof(uint32_t), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *(volatile uint32_t *)h_abort = 0u;
+        e = cudaHostGetDevicePointer(&d_abort, h_abort, 0);
+    }
     for (Slot &q : slot) {
         if (e == cudaSuccess) e = cudaMalloc(&q.d_out, (size_t)batch * owords * 4u);
         if (e == cudaSuccess) e = cudaMalloc(&q.d_len, (size_t)batch * 4u);
@@ -304,11 +312,11 @@ extern "C" mtgp_status mtgp_params_search_gpu(uint32_t mexp, uint64_t seed0, uin
             e = cudaMemcpyAsync(d_seq, seq.data(), (size_t)nb * w64 * 8u, cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) e = launch_bm(d_seq, (uint32_t)nb, (uint32_t)n, words, q.d_out, owords, q.d_len, s);
             if (e == cudaSuccess)
-                e = launch_irr(q.d_out, (uint32_t)nb, owords, q.d_len, mexp, kIrrSieve, 0u, q.d_ver, s);
+                e = launch_irr(q.d_out, (uint32_t)nb, owords, q.d_len, mexp, kIrrSieve, 0u, nullptr, q.d_ver, s);
             if (e == cudaSuccess) e = cudaEventRecord(q.sieved, s);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(q.sf, q.sieved, 0);
             if (e == cudaSuccess)
-                e = launch_irr(q.d_out, (uint32_t)nb, owords, q.d_len, mexp, kIrrSieve, 1u, q.d_ver, q.sf);
+                e = launch_irr(q.d_out, (uint32_t)nb, owords, q.d_len, mexp, kIrrSieve, 1u, d_abort, q.d_ver, q.sf);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(q.h_ver, q.d_ver, (size_t)nb * 4u, cudaMemcpyDeviceToHost, q.sf);
             if (e == cudaSuccess) e = cudaEventRecord(q.settled, q.sf);
@@ -362,8 +370,10 @@ extern "C" mtgp_status mtgp_f2_irreducible_gpu(const uint64_t *polys, uint32_t c
     try {
         std::vector<uint32_t> ver(count);
         e = cudaMemcpyAsync(d_polys, polys, bytes, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = launch_irr(d_polys, count, 2u * words, nullptr, p, kIrrSieve, 0u, d_ver, s);
-        if (e == cudaSuccess) e = launch_irr(d_polys, count, 2u * words, nullptr, p, kIrrSieve, 1u, d_ver, s);
+        if (e == cudaSuccess)
+            e = launch_irr(d_polys, count, 2u * words, nullptr, p, kIrrSieve, 0u, nullptr, d_ver, s);
+        if (e == cudaSuccess)
+            e = launch_irr(d_polys, count, 2u * words, nullptr, p, kIrrSieve, 1u, nullptr, d_ver, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ver.data(), d_ver, (size_t)count * 4u, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail_cuda(e, "test");

@@ -86,7 +86,7 @@ def test_gpu_irreducibility_equals_the_oracle(M, p):
     known = len(polys)                                        # the polynomials above are irreducible
     nrand = 160 if p <= 127 else 24
     polys += [_poly(p, rng) for _ in range(nrand)]
-    # products with a factor of each degree 2 .. 45 (the sieve finds those of degree <= 20)
+    # products with a factor of each degree 2 .. 45 (the sieve finds those of degree <= 40)
     for d in [d for d in (range(2, 46) if p <= 607 else (2, 17, 40, 41, 45)) if d < p - 1]:
         f, g = _poly(d, rng, False), _poly(p - d, rng, False)
         polys.append((np.convolve(f, g) % 2).astype(np.uint8))

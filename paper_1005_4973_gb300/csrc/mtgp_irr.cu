@@ -100,7 +100,7 @@ __device__ __forceinline__ int top_degree(const uint32_t *a, int maxdeg)
 // Shared scratch of one block.
 struct IrrShared {
     uint64_t *V;       // 2W products of a multiplication
-    uint64_t *tq;      // 16: q * n
+    uint64_t *tq;      // 2 x 16: q * n, by window parity
     uint32_t *phi;     // W (+2)
     uint32_t *r;       // W: x^(2^k) mod phi
     uint32_t *acc;     // W: the sieve's product
@@ -112,38 +112,54 @@ struct IrrShared {
     uint32_t W;
 };
 
+// Warp 0: the quotient digit of the window at bit s of a and its nibble
+// table, published in the slots of parity `par`.
+__device__ __forceinline__ void publish_digit(const IrrShared &S, const uint32_t *a, uint32_t s, uint32_t h,
+                                              bool fixed, uint32_t par)
+{
+    const uint32_t lane = threadIdx.x;
+    const uint32_t w = bits32_at(a, s);
+    const uint32_t q = fixed ? S.qt[w & 255u] ^ S.qt[256u + ((w >> 8) & 255u)] ^ S.qt[512u + ((w >> 16) & 255u)] ^
+                                   S.qt[768u + (w >> 24)]
+                             : solve_digit(w, h);
+    if (lane < 16u) S.tq[16u * par + lane] = clmul_nibble(q, lane);
+    if (lane == 0u) S.sq[par] = q;
+}
+
 // a mod b in place: a of degree <= da, b of degree db >= 1, a's array holding
 // word (da - db) / 32 + db / 32 + 1.  Afterwards a has degree < db.  With
 // `fixed`, b is phi and the digit comes from the tables; otherwise it is
-// solved bit by bit.  Warp 0 finds the digit and tabulates q * n; a window
-// takes two block barriers: the digit is published (and the window's bits
-// read) before any thread writes, and every write is done before the next
-// window is read.  The digit's slot alternates with the window's parity, so a
-// window whose digit is 0 needs no second barrier.
+// solved bit by bit.  Thread t updates the words Wb - t, Wb - t - 512, ... of
+// the window's product (Wb = db / 32 + 1), so the two words that hold the
+// next window's bits are written by warp 0 alone: warp 0 finds the next digit
+// as soon as its own writes are done, while the other warps finish theirs,
+// and one block barrier per window publishes the digit (digit and nibble
+// table alternate between two slots by window parity).
 __device__ void blk_reduce(const IrrShared &S, uint32_t *a, int da, const uint32_t *b, uint32_t db, bool fixed)
 {
     const uint32_t tid = threadIdx.x;
     if (da < (int)db) return;
     const uint32_t h = top32_below(b, db);
     const uint32_t Wb = db / 32u + 1u;
-    for (int k = (int)((uint32_t)da - db) / 32; k >= 0; --k) {
-        const uint32_t s = db + 32u * (uint32_t)k;
-        if (tid < 32u) {
-            const uint32_t w = bits32_at(a, s);
-            const uint32_t q = fixed ? S.qt[w & 255u] ^ S.qt[256u + ((w >> 8) & 255u)] ^
-                                           S.qt[512u + ((w >> 16) & 255u)] ^ S.qt[768u + (w >> 24)]
-                                     : solve_digit(w, h);
-            if (tid < 16u) S.tq[tid] = clmul_nibble(q, tid);
-            if (tid == 0) S.sq[k & 1] = q;
+    const int kmax = (int)((uint32_t)da - db) / 32;
+    if (tid < 32u) publish_digit(S, a, db + 32u * (uint32_t)kmax, h, fixed, (uint32_t)kmax & 1u);
+    __syncthreads();
+    for (int k = kmax; k >= 0; --k) {
+        const uint32_t par = (uint32_t)k & 1u;
+        const uint32_t q = S.sq[par];                          // uniform
+        if (q != 0u) {                                         // a ^= (q b) x^(32 k)
+            const uint64_t *tq = S.tq + 16u * par;
+            for (uint32_t i = tid; i <= Wb; i += kIrrThreads) {
+                const uint32_t m = Wb - i;
+                uint32_t v = 0;
+                if (m < Wb) v = (uint32_t)clmul_q(tq, b[m]);
+                if (m > 0u) v ^= (uint32_t)(clmul_q(tq, b[m - 1u]) >> 32);
+                a[(uint32_t)k + m] ^= v;
+            }
         }
-        __syncthreads();
-        const uint32_t q = S.sq[k & 1];
-        if (q == 0u) continue;                                  // uniform
-        for (uint32_t m = tid; m <= Wb; m += kIrrThreads) {     // a ^= (q b) x^(32 k)
-            uint32_t v = 0;
-            if (m < Wb) v = (uint32_t)clmul_q(S.tq, b[m]);
-            if (m > 0u) v ^= (uint32_t)(clmul_q(S.tq, b[m - 1u]) >> 32);
-            a[(uint32_t)k + m] ^= v;
+        if (k > 0 && tid < 32u) {                              // the next window's bits: warp 0's words
+            __syncwarp();
+            publish_digit(S, a, db + 32u * (uint32_t)(k - 1), h, fixed, par ^ 1u);
         }
         __syncthreads();
     }
@@ -221,7 +237,7 @@ __global__ void __launch_bounds__(kIrrThreads, 2) k_irr(const uint32_t *__restri
     S.W = W;
     S.V = reinterpret_cast<uint64_t *>(smem);
     S.tq = S.V + 2u * W;
-    S.phi = reinterpret_cast<uint32_t *>(S.tq + 16);
+    S.phi = reinterpret_cast<uint32_t *>(S.tq + 32);
     S.r = S.phi + W + 2u;
     S.acc = S.r + W;
     S.t = S.acc + W;
@@ -335,7 +351,7 @@ __global__ void __launch_bounds__(kIrrThreads, 2) k_irr(const uint32_t *__restri
 size_t irr_smem_bytes(uint32_t p)
 {
     const size_t W = p / 32u + 1u;
-    return 8u * (2u * W + 16u) + 4u * ((W + 2u) + W + W + (2u * W + 2u) + 2u * (W + 2u) + 1024u + 32u + 2u);
+    return 8u * (2u * W + 32u) + 4u * ((W + 2u) + W + W + (2u * W + 2u) + 2u * (W + 2u) + 1024u + 32u + 2u);
 }
 
 cudaError_t launch_irr(const uint32_t *polys, uint32_t count, uint32_t words, const uint32_t *deg, uint32_t p,

@@ -18,10 +18,11 @@
 // product is a sum of 32 x 32 carry-less word products.  Reduction modulo a
 // divisor b of degree db runs from the top in 32-bit windows [db + 32k,
 // db + 32k + 32): the window's bits w determine the 32-bit quotient digit q
-// by the triangular system w = q + (q * h) >> 32 with h the 32 coefficients of
-// b below its leading one, then a ^= (q * b) x^(32k) clears the window.  For
-// phi the map w -> q (linear) is tabulated once per block, four byte-indexed
-// tables; for the gcd's changing divisors every thread solves it bit by bit.
+// by the triangular system w = q ^ ((q (x) h) >> 32), (x) the carry-less
+// product and h the 32 coefficients of b below its leading one; then
+// a ^= (q (x) b) x^(32k) clears the window.  For phi the map w -> q (linear)
+// is tabulated once per block, four byte-indexed tables; for the gcd's
+// changing divisors warp 0 solves it bit by bit.
 #include "mtgp_internal.h"
 
 namespace mtgp {

@@ -116,3 +116,21 @@ def test_gpu_irreducibility_rejects_bad_arguments(M):
         M.mtgp_f2_irreducible_gpu([c[:32]], 31)            # too small
     with pytest.raises(M.MTGPError):
         M.mtgp_f2_irreducible_gpu([], 89)                  # no polynomial
+
+
+def test_gpu_irreducibility_of_products_beyond_one_block_pass(M):
+    """p = 19937: the polynomial has more words than the block has threads,
+    so every reduction window's update loops.  Products with a factor of
+    degree 3, 29 and 43 are reducible; a polynomial of degree p + 1 is
+    rejected."""
+    p = 19937
+    rng = np.random.default_rng(7)
+    polys = []
+    for d in (3, 29, 43):
+        f, g = _poly(d, rng), _poly(p - d, rng)
+        polys.append((np.convolve(f, g) % 2).astype(np.uint8))
+    over = np.zeros(p + 2, dtype=np.uint8)
+    over[0] = over[p + 1] = over[5] = 1
+    polys.append(over)
+    got = M.mtgp_f2_irreducible_gpu(polys, p)
+    assert not got.any()

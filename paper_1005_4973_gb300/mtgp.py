@@ -37,8 +37,9 @@ def mtgp_params_search(mexp: int, seed0: int, gen_id: int, max_tries: int = 1 <<
 
 def mtgp_params_search_gpu(mexp: int, seed0: int, gen_id: int, max_tries: int = 1 << 20, threads: int = 0,
                            stream=None):
-    """The Sec. 5 recursion-parameter search with Berlekamp-Massey on the GPU
-    (one warp per candidate); the same result as mtgp_params_search."""
+    """The Sec. 5 recursion-parameter search with its polynomial work on the
+    GPU (Berlekamp-Massey, one warp per candidate; irreducibility, one block
+    per candidate); the same result as mtgp_params_search."""
     p = mtgp_params()
     found, tries = ctypes.c_uint64(), ctypes.c_uint64()
     words = np.zeros(mexp // 64 + 1, dtype=np.uint64)

@@ -512,3 +512,32 @@ def test_flow_form_bounded_wait_runs_out_and_reports():
     pool.generate([(0, 0, 1000, 0)], out)               # the first pool also runs again, without errors
     torch.cuda.synchronize()
     assert pool.errors() == 0
+
+
+def test_more_than_2_32_numbers_in_one_request():
+    """One request of 2^32 + 12345 numbers (16 GiB of output, split into
+    jump-ahead pieces): positions, output offsets and the state write-back
+    past 32 bits.  The last 2^20 numbers and the final state equal the
+    oracle's, which generates the whole stream in 2^28-number parts."""
+    n = (1 << 32) + 12345
+    g = WL.GenSpec(11213, 21, 21, 21)
+    pool = lib_pool([g])
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    pool.generate([(0, WL.U32, n, 0)], out)
+    torch.cuda.synchronize()
+    tail = as_u32(out[n - (1 << 20):])
+    head = as_u32(out[:4096])
+    del out
+    torch.cuda.empty_cache()
+    p, st = oracle_state(g)
+    first = O.generate(p, st, 4096, WL.U32)
+    left = n - 4096
+    while left > (1 << 20):
+        k = min(1 << 28, left - (1 << 20))
+        O.generate(p, st, k, WL.U32)
+        left -= k
+    last = O.generate(p, st, left, WL.U32)
+    assert np.array_equal(head, first)
+    assert np.array_equal(tail, last)
+    assert np.array_equal(pool.read_state(0), st)
+    assert pool.position(0) == n

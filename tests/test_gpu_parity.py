@@ -541,3 +541,40 @@ def test_more_than_2_32_numbers_in_one_request():
     assert np.array_equal(tail, last)
     assert np.array_equal(pool.read_state(0), st)
     assert pool.position(0) == n
+
+
+@pytest.mark.parametrize("pieces", [1, 0])
+def test_zero_state_is_a_fixed_point(pieces):
+    """The degenerate case of the recursion: a state whose p effective bits
+    are all zero (here with the r bits the mask drops set in x_0) is a fixed
+    point; loaded from a checkpoint it generates zero words, 1.0f and 0.0f, as
+    the oracle does, with and without jump-ahead pieces."""
+    import paper_1005_4973_gb300 as M
+    gens = [WL.GenSpec(11213, 31, 31, 31), WL.GenSpec(23209, 32, 32, 32)]
+    pool = lib_pool(gens)
+    pool.set_config(pieces=pieces)
+    blob = bytearray(pool.save())
+    nst = sum((oracle_params(g).N + 3) & ~3 for g in gens)   # states start 16-byte aligned
+    words = np.frombuffer(blob, dtype=np.uint32, count=nst, offset=len(blob) - 4 * nst).copy()
+    ops, off = [], 0
+    for g in gens:
+        p = oracle_params(g)
+        words[off:off + p.N] = 0
+        words[off] = ~np.uint32(p.mask)                  # bits outside the p effective ones
+        ops.append((p, words[off:off + p.N].copy()))
+        off += (p.N + 3) & ~3
+    blob[len(blob) - 4 * nst:] = words.tobytes()
+    pool.load(bytes(blob))
+    n = 1 << 20
+    reqs = [(0, WL.U32, n, 0), (1, WL.F12, n, n), (0, WL.F01, n, 2 * n)]
+    out = torch.full((3 * n,), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    pool.generate(reqs, out)
+    torch.cuda.synchronize()
+    got = as_u32(out)
+    assert pool.errors() == 0
+    st0, st1 = ops[0][1].copy(), ops[1][1].copy()
+    ref = [O.generate(ops[0][0], st0, n, WL.U32), O.generate(ops[1][0], st1, n, WL.F12),
+           O.generate(ops[0][0], st0, n, WL.F01)]
+    assert not ref[0].any() and (ref[1] == 0x3F800000).all() and not ref[2].any()
+    for (g, dt, k, o), r in zip(reqs, ref):
+        assert np.array_equal(got[o:o + k], r), (g, dt)

@@ -554,10 +554,29 @@ def main():
         for _ in range(args.e2e_steps):
             pool.generate_host(reqs, host)
         dt = time.perf_counter() - t0
+        # the host link on this machine: device-to-host copies of the same bytes into the same pinned
+        # buffer, in two halves on two streams (two copy engines), best of three -- the ceiling
+        # the end-to-end figure runs against
+        dev = torch.empty(total, dtype=torch.int32, device="cuda")
+        half = total // 2
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        link_gbs = 0.0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            for k, st in enumerate(streams):
+                with torch.cuda.stream(st):
+                    sl = slice(0, half) if k == 0 else slice(half, total)
+                    host[sl].copy_(dev[sl], non_blocking=True)
+            torch.cuda.synchronize()
+            link_gbs = max(link_gbs, 4 * total / (time.perf_counter() - t1) / 1e9)
+        del dev
         e2e = {"value": total * args.e2e_steps / dt / 1e9, "unit": "Gnum/s",
                "h2d_bytes_per_step": 64 * len(reqs), "d2h_bytes_per_step": 4 * total,
                "steps": args.e2e_steps, "warmup": max(args.warmup, 3),
-               "path": "mtgp_pool_generate_host into pinned host memory"}
+               "path": "mtgp_pool_generate_host into pinned host memory",
+               "link_probe_gbs": link_gbs,
+               "frac_of_link": 4 * total * args.e2e_steps / dt / 1e9 / link_gbs}
         del host
 
     cpu = None

@@ -110,7 +110,10 @@ typedef struct mtgp_config {
                                   split 128, 256, 512, 1024 (at most 12, 11, 6, 3);
                                   flow 128, 256, 512, 1024 (at most 12, 11, 6, 8);
                                   wide 96, 128, 192 (rounds of at most 1529 words);
-                                  pairs 128 (at most 6 pairs); dual 128 (3)         */
+                                  pairs 128 (at most 6 pairs); dual 128 (3).  Plain
+                                  form: a launch whose rounds need more columns
+                                  than this size has a kernel for runs with the
+                                  smallest larger size that has one (256, 512)    */
     uint32_t persistent;       /* 1 (default): grid of SMs x blocks_per_sm blocks
                                   taking work items longest first from a device
                                   counter; 0: one block per work item               */

@@ -453,7 +453,7 @@ mtgp_status launch_shape_wide(const mtgp_pool *p, const mtgp_config &c, const ui
     return MTGP_OK;
 }
 
-mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_t *gens, size_t n, size_t items,
+mtgp_status launch_shape(const mtgp_pool *p, mtgp_config &c, const uint32_t *gens, size_t n, size_t items,
                          uint32_t *qmax_out, uint32_t *B_out)
 {
     uint32_t nmax = 0, smax = 0;
@@ -462,6 +462,15 @@ mtgp_status launch_shape(const mtgp_pool *p, const mtgp_config &c, const uint32_
         nmax = std::max(nmax, g.N);
         smax = std::max(smax, g.N - g.M);
     }
+    // plain form: rounds longer than the configured block size has a kernel
+    // for (exponents above 44497) run with the smallest larger block size that
+    // has one
+    if (c.form == 0u && !kernel_slots(c.threads, 0u, (smax + c.threads - 1u) / c.threads))
+        for (uint32_t t : {256u, 512u})
+            if (t > c.threads && kernel_slots(t, 0u, (smax + t - 1u) / t)) {
+                c.threads = t;
+                break;
+            }
     if (c.form == 3u) return launch_shape_wide(p, c, gens, n, items, nmax, smax, qmax_out, B_out);
     // columns a slot covers: one per thread (plain, dual), one per thread of
     // the recursion half (split, flow), two per thread (pairs)

@@ -578,3 +578,34 @@ def test_zero_state_is_a_fixed_point(pieces):
     assert not ref[0].any() and (ref[1] == 0x3F800000).all() and not ref[2].any()
     for (g, dt, k, o), r in zip(reqs, ref):
         assert np.array_equal(got[o:o + k], r), (g, dt)
+
+
+@pytest.mark.parametrize("pieces", [0, 1])
+def test_largest_exponents_with_the_default_configuration(pieces):
+    """MTGP86243 and MTGP110503 (N = 2696 and 3454: rounds longer than the
+    128-thread kernels cover) generate with the default configuration (the
+    plain form moves to a larger block size), mixed with an MTGP11213
+    generator, over two calls, with jump-ahead pieces (the few-item rule
+    splits these launches) and without, and match the oracle."""
+    gens = [WL.GenSpec(86243, 3, 3, 3), WL.GenSpec(110503, 4, 4, 4), WL.GenSpec(11213, 5, 5, 5)]
+    pool = lib_pool(gens)
+    pool.set_config(pieces=pieces)
+    spec = [(0, WL.U32, 300001), (1, WL.F01, 250003), (2, WL.F12, 99999), (1, WL.U32, 7)]
+    reqs, off = [], 0
+    for g, dt, n in spec:
+        reqs.append((g, dt, n, off))
+        off += n
+    out = torch.full((off,), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    pool.generate(reqs, out)
+    pool.generate(reqs, out)                             # the second call continues the streams
+    torch.cuda.synchronize()
+    got = as_u32(out)
+    sts = {g: oracle_state(gens[g]) for g in range(3)}
+    for rep in range(2):
+        for g, dt, n, o in reqs:
+            p, st = sts[g]
+            ref = O.generate(p, st, n, dt)
+            if rep == 1:
+                assert np.array_equal(got[o:o + n], ref), (g, dt, n)
+    for g in range(3):
+        assert np.array_equal(pool.read_state(g), sts[g][1])

@@ -198,8 +198,15 @@ def test_too_small_buffer_rejected():
     with pytest.raises(M.MTGPError):
         pool.generate([(0, 0, 16, 0)], out)
     pool.set_config(buffer_words=0, threads=32)
-    big = lib_pool([MIXED[2]])                      # S > 32 x 11: no 32-thread shape
+    # S > 32 x 11: no 32-thread kernel; the plain form runs the launch with the
+    # next block size that has one, and the output is the oracle's
+    big = lib_pool([MIXED[2]])
     big.set_config(threads=32)
+    out2 = torch.zeros(5000, dtype=torch.int32, device="cuda")
+    big.generate([(0, 0, 5000, 0)], out2)
+    p2, st2 = oracle_state(MIXED[2])
+    assert np.array_equal(as_u32(out2), O.generate(p2, st2, 5000, 0))
+    big.set_config(threads=128, form=5)             # the dual form has no kernel for these rounds
     with pytest.raises(M.MTGPError):
         big.generate([(0, 0, 16, 0)], out)
 
